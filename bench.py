@@ -1,0 +1,350 @@
+"""Training throughput of the one-hidden-layer sigmoid network (arXiv 1908.07847)
+on one or more GB300s: train sample-steps/s (forward + backward + update).
+
+Default workload (one line of JSON on rank 0): the 33-64-1 network trained by
+full-batch gradient descent (lr 0.1, mean squared error) on 4096 synthetic rows
+x 33 standardised markers with teacher-net labels.  One step is one epoch: one
+pass of forward, output error, backpropagation, cross-block reduction and
+update over the 4096 rows, through the C ABI (mlp_train_epochs).  L2 is flushed
+(256 MiB write) between timed steps, outside the timed intervals; every step is
+timed with CUDA events on the launching stream.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle on the host cores (the reference
+arm of this benchmark: the serial program the paper's 50x speedup is quoted
+against, written from the paper).  With --gpus N > 1 (under torchrun) every rank
+trains its own replica on its own seeded data; no data crosses ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N_ROWS, D_IN, H_HID, LR = 4096, 33, 64, 0.1
+WORKLOAD = "33-64-1 sigmoid MLP, full-batch GD lr 0.1, 4096 rows x 33 features, FP32"
+METRIC = "train sample-steps/s (fwd+bwd+update) vs plain FP32 path on 1 GB300; % roofline"
+FLOPS_PER_SAMPLE = 4 * D_IN * H_HID + 10 * H_HID   # forward 2DH+3H, backward 2DH+7H
+SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+FUSED_SRC = os.path.join(ROOT, "paper_1908_07847_gb300", "csrc", "fused_kernels.cu")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def aggregate_max(value: float, world: int) -> float:
+    """Max of a per-rank float over all ranks (identity when world == 1)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ------------------------------------------------------------------ inputs --
+
+def workload_inputs(rank: int):
+    """Seeded synthetic rows (features N(0,1)), weights and teacher weights;
+    labels are computed afterwards by the library's own predict call."""
+    from paper_1908_07847_gb300 import inputs as I
+    X = I.features(I.COHORT_SEED + 1 + 1000 * rank, N_ROWS, D_IN)
+    W = I.init_weights(I.INIT_SEED + rank, D_IN, H_HID)
+    T = I.teacher_weights(D=D_IN)
+    return X, W, T
+
+
+# ---------------------------------------------------------------- clocks ----
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples while the timed loop runs."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------- our arm ------
+
+def traffic_from_profile():
+    """DRAM bytes per launch of the fused kernel from the committed ncu summary,
+    if it was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        rec = json.load(open(path))
+        src = hashlib.sha256(open(FUSED_SRC, "rb").read()).hexdigest()[:16]
+        if rec.get("source_sha256_16") == src and rec.get("workload") == WORKLOAD:
+            return rec.get("dram_bytes_per_launch")
+    except Exception:
+        pass
+    return None
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    from paper_1908_07847_gb300 import binding as B
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream().cuda_stream
+    X, W, T = workload_inputs(rank)
+    Xd = torch.from_numpy(X).to(dev)
+    # labels: the teacher net's class decisions, by the library's predict
+    th = B.mlp_create(D_IN, T[0].shape[0], LR, 1, B.MLP_FP32, B.MLP_ACT_SIGMOID)
+    B.mlp_set_weights(th, *T)
+    lab = torch.zeros(N_ROWS, dtype=torch.int8, device=dev)
+    B.mlp_predict(th, Xd, N_ROWS, lab, stream)
+    B.mlp_destroy(th)
+    yd = lab.to(torch.float32)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def timed(step_fn, steps, warmup):
+        for _ in range(warmup):
+            step_fn()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for s, e in ev:
+            flush.zero_()
+            s.record()
+            step_fn()
+            e.record()
+        torch.cuda.synchronize()
+        return [s.elapsed_time(e) * 1e-3 for s, e in ev]
+
+    h = B.mlp_create(D_IN, H_HID, LR, 1, B.MLP_FP32, B.MLP_ACT_SIGMOID)
+    hp = B.mlp_create(D_IN, H_HID, LR, 1, B.MLP_FP32, B.MLP_ACT_SIGMOID)
+    B.mlp_set_weights(h, *W)
+    B.mlp_set_weights(hp, *W)
+    loss = torch.zeros(1, dtype=torch.float64, device=dev)
+
+    def fused_step():
+        B.mlp_train_epochs(h, Xd, yd, N_ROWS, 1, 0, loss, None, stream)
+
+    def plain_step():
+        B.mlp_step_plain(hp, Xd, yd, N_ROWS, loss, stream)
+
+    # e2e: host buffers through the C ABI (pinned), copies inside the timed step
+    Xh = torch.from_numpy(X).pin_memory()
+    yh = yd.cpu().pin_memory()
+    lh = torch.zeros(1, dtype=torch.float64).pin_memory()
+    he = B.mlp_create(D_IN, H_HID, LR, 1, B.MLP_FP32, B.MLP_ACT_SIGMOID)
+    B.mlp_set_weights(he, *W)
+
+    def e2e_step():
+        B.mlp_train_host(he, Xh, yh, N_ROWS, 1, 0, lh, stream)
+
+    barrier(world)
+    with ClockSampler(local) as clk:
+        t_fused = timed(fused_step, args.steps, args.warmup)
+    t_plain = timed(plain_step, max(args.steps // 4, 10), args.warmup)
+    t_e2e = timed(e2e_step, max(args.steps // 4, 10), args.warmup)
+    assert B.mlp_check(h, stream) == B.MLP_OK, B.mlp_last_error()
+    for x in (h, hp, he):
+        B.mlp_destroy(x)
+    barrier(world)
+    T_f = aggregate_max(sum(t_fused), world)
+    T_p = aggregate_max(sum(t_plain), world)
+    T_e = aggregate_max(sum(t_e2e), world)
+    units = N_ROWS * world
+    value = units * args.steps / T_f
+    plain_value = units * len(t_plain) / T_p
+    e2e_value = units * len(t_e2e) / T_e
+    clocks = clk.summary()
+    launch_s = statistics.mean(t_fused)
+    achieved = FLOPS_PER_SAMPLE * N_ROWS / launch_s / 1e12
+    peak = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    out = {
+        "metric": METRIC, "value": value, "unit": "sample-steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": T_f / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (N(0,1) features, teacher-net labels; the paper's cohort is not public)",
+        "config": {"workload": WORKLOAD, "n": N_ROWS, "D": D_IN, "H": H_HID, "lr": LR,
+                   "step": "one full-batch epoch: fwd+bwd+reduction+update (fused cooperative kernel)",
+                   "l2": "flushed between timed steps (256 MiB write, outside the timed intervals)"},
+        "plain_fp32": {"value": plain_value, "unit": "sample-steps/s",
+                       "ms_per_step": T_p / len(t_plain) * 1e3,
+                       "path": "separate forward/output/gradient/reduce/update kernels (mlp_step_plain)",
+                       "speedup_of_fused": value / plain_value},
+        "e2e": {"value": e2e_value, "unit": "sample-steps/s",
+                "h2d_bytes_per_step": N_ROWS * D_IN * 4 + N_ROWS * 4, "d2h_bytes_per_step": 8,
+                "call": "mlp_train_host (pinned host X, y in; loss out)"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": traffic_from_profile(),
+                     "kernel": "k_fused_train<36,2,sigmoid>",
+                     "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (FFMA, derived)",
+                     "flops_per_launch": FLOPS_PER_SAMPLE * N_ROWS},
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+    }
+    if rank == 0:
+        out["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(out), flush=True)
+
+
+# ------------------------------------------------------- reference arm ------
+
+def oracle_epoch_rate(budget_s: float, rows: int):
+    """Times the FP64 oracle on full-batch epochs of `rows` rows of the
+    workload for about budget_s seconds; returns (sample-steps/s, epochs, rows)."""
+    import oracle
+    from paper_1908_07847_gb300 import inputs as I
+    X, W, T = workload_inputs(0)
+    X = X[:rows]
+    y = oracle.predict(X, oracle.Params(*T)).astype(np.float64)
+    p = oracle.Params(*W)
+    t0 = time.perf_counter()
+    oracle.train(X, y, p, LR, 1)
+    one = max(time.perf_counter() - t0, 1e-6)
+    epochs = max(1, int(budget_s / one))
+    t0 = time.perf_counter()
+    oracle.train(X, y, p, LR, epochs)
+    dt = time.perf_counter() - t0
+    return rows * epochs / dt, epochs, rows
+
+
+def cpu_baseline():
+    rate, epochs, rows = oracle_epoch_rate(10.0, N_ROWS)
+    return {"value": rate, "unit": "sample-steps/s", "cores": 1, "kind": "oracle",
+            "sample": "%d full-batch epochs over all %d rows (serial FP64 C oracle, one thread)" % (epochs, rows)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+    from paper_1908_07847_gb300 import inputs as I
+    X, W, T = workload_inputs(0)
+    y = oracle.predict(X, oracle.Params(*T)).astype(np.float64)
+    p = oracle.Params(*W)
+    # Each step: one full-batch epoch over a bounded slice of the rows, sized so
+    # that warm-up + steps take about two minutes at most.
+    t0 = time.perf_counter()
+    oracle.train(X, y, p, LR, 1)
+    one = time.perf_counter() - t0
+    rows = N_ROWS
+    total = (args.steps + args.warmup) * one
+    if total > 120.0:
+        rows = max(64, int(N_ROWS * 120.0 / total))
+    Xs, ys = X[:rows], y[:rows]
+    for _ in range(args.warmup):
+        p, _, _ = oracle.train(Xs, ys, p, LR, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        p, lh, _ = oracle.train(Xs, ys, p, LR, 1)
+    dt = time.perf_counter() - t0
+    value = rows * args.steps / dt
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "sample-steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (N(0,1) features, teacher-net labels)",
+        "config": {"workload": WORKLOAD, "n": N_ROWS, "D": D_IN, "H": H_HID, "lr": LR,
+                   "step": "one full-batch epoch over %d of the %d rows (FP64 C oracle)" % (rows, N_ROWS)},
+        "cpu_baseline": {"value": value, "unit": "sample-steps/s", "cores": 1, "kind": "oracle",
+                         "sample": "%d steps of one full-batch epoch over %d rows" % (args.steps, rows)},
+        "e2e": {"value": value, "unit": "sample-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if world > 1 and args.impl == "ours":
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local)
+    if world > 1 and args.impl == "ours":
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

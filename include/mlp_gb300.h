@@ -1,0 +1,213 @@
+/*
+ * mlp_gb300.h -- C ABI of the GB300 (sm_103a) training library for the
+ * one-hidden-layer feed-forward network of Ramroach et al., "CUDA optimized
+ * Neural Network predicts blood glucose control from quantified joint mobility
+ * and anthropometrics" (arXiv 1908.07847).
+ *
+ * The method (Sec. 2.2 and Eq. 1 of the paper):
+ *   forward    z1 = X W1^T + b1,  h = f(z1),  z2 = h w2 + b2,  o = sigmoid(z2)
+ *              with sigmoid(x) = 1 / (1 + e^-x) (Eq. 1) and f = sigmoid (or tanh,
+ *              the other activation Sec. 2.2 names);
+ *   error      the difference o - y between outputs and true values (Sec. 2.2);
+ *              loss E = (c/2) sum_i (o_i - y_i)^2, c = 1/n (loss_mean = 1) or 1;
+ *   backward   d2 = dE/do * o (1 - o),  d1 = (d2 w2^T) .* f'(h),
+ *              gW1 = d1^T X, gb1 = sum_i d1, gw2 = h^T d2, gb2 = sum_i d2;
+ *   update     gradient descent without momentum, w <- w - lr g (Sec. 2.2,
+ *              lr = 0.1 in the paper);
+ *   classify   label = 1 iff o >= 0.5 (Sec. 2.2: the test rows are classified).
+ *
+ * Layouts (Sec. 2.2: the input is one flat array of rows x columns, each
+ * layer's weights one flat array of hidden x columns):
+ *   X   n x D row-major; element type float (MLP_FP32), bfloat16 bits as
+ *       uint16_t (MLP_BF16; padding columns must hold 0) or double (MLP_FP64).
+ *   y   n labels, float (double for MLP_FP64), normally 0 or 1.
+ *   W1  H x D row-major (neuron j's D incoming weights contiguous), b1 [H],
+ *       w2 [H], b2 [1]; float for MLP_FP32 / MLP_BF16 (FP32 master weights),
+ *       double for MLP_FP64.  Packed parameter vector order, where one is used:
+ *       [W1, b1, w2, b2], (D + 2) H + 1 values.
+ *   o   n outputs, float (double for MLP_FP64).
+ *
+ * Conventions for every call:
+ *   - Pointers named *_host are host memory; every other data pointer is device
+ *     memory on the current CUDA device.  The caller owns every buffer it
+ *     passes; the library only borrows it for the duration of the call.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls are
+ *     asynchronous on that stream unless they read or write host memory; those
+ *     synchronise the stream before returning.
+ *   - Every call returns an mlp_status and never aborts the process.  On
+ *     MLP_EINVAL nothing has been launched and no output has been written.  The
+ *     message of the last failure on the calling thread is in mlp_last_error().
+ *   - Kernels that wait on one another across thread blocks give up after about
+ *     one second; they then record MLP_ETIMEOUT in the handle's device status,
+ *     which mlp_check() returns.  Non-finite losses record MLP_ENONFINITE.
+ *   - n = 0 is valid: outputs of size n are untouched, gradients are zero,
+ *     an update with zero gradients leaves the weights unchanged.
+ */
+#ifndef MLP_GB300_H
+#define MLP_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mlp_net *mlp_t;
+
+typedef enum {
+    MLP_OK = 0,
+    MLP_EINVAL = 1,       /* bad argument (null pointer, size, precision) */
+    MLP_ENOMEM = 2,       /* device or host allocation failed */
+    MLP_ECUDA = 3,        /* a CUDA runtime call failed */
+    MLP_ETIMEOUT = 4,     /* a cross-block wait gave up (see mlp_check) */
+    MLP_ENONFINITE = 5,   /* a loss became NaN or infinite (see mlp_check) */
+    MLP_EUNSUPPORTED = 6  /* valid request that this build does not implement */
+} mlp_status;
+
+typedef enum { MLP_FP32 = 0, MLP_BF16 = 1, MLP_FP64 = 2 } mlp_precision;
+typedef enum { MLP_ACT_SIGMOID = 0, MLP_ACT_TANH = 1 } mlp_activation;
+
+/* Network shape and training constants (Sec. 2.2). */
+typedef struct {
+    int32_t D;         /* inputs per row, 1..4096 */
+    int32_t H;         /* hidden units, 1..65536 */
+    float lr;          /* learning rate (the paper uses 0.1) */
+    int32_t loss_mean; /* 1: c = 1/n (mean squared error / 2); 0: c = 1 */
+    int32_t prec;      /* mlp_precision of X and of the arithmetic */
+    int32_t act;       /* mlp_activation of the hidden layer */
+} mlp_config;
+
+/* Create a network on the current device.  The handle owns its FP32 (FP64 for
+ * MLP_FP64) master weights, initialised to zero, and its scratch buffers.
+ * Returns MLP_EINVAL for an out-of-range field, MLP_ENOMEM if the weights
+ * cannot be allocated. */
+mlp_status mlp_create(const mlp_config *cfg, mlp_t *out);
+
+/* Free the handle and everything it owns.  NULL is ignored. */
+void mlp_destroy(mlp_t net);
+
+/* Copy weights from / to host memory (W1 H x D row-major, b1 [H], w2 [H],
+ * b2 [1]; float, or double for MLP_FP64).  Synchronous. */
+mlp_status mlp_set_weights(mlp_t net, const void *W1_host, const void *b1_host,
+                           const void *w2_host, const void *b2_host);
+mlp_status mlp_get_weights(mlp_t net, void *W1_host, void *b1_host,
+                           void *w2_host, void *b2_host);
+
+/* Device address of the handle's packed weights [W1, b1, w2, b2] (valid until
+ * mlp_destroy). */
+mlp_status mlp_weights_device(mlp_t net, void **params_dev);
+
+/* Forward pass (Sec. 2.2, Eq. 1) with the handle's weights: writes o [n]. */
+mlp_status mlp_forward(mlp_t net, const void *X, int64_t n, void *o, void *stream);
+
+/* Squared-error gradients at the handle's weights (Sec. 2.2 backpropagation):
+ * writes gW1 [H x D], gb1 [H], gw2 [H], gb2 [1] (float; double for MLP_FP64)
+ * and, if loss != NULL, the FP64 loss E on the device.  Does not update. */
+mlp_status mlp_backward(mlp_t net, const void *X, const void *y, int64_t n,
+                        void *gW1, void *gb1, void *gw2, void *gb2,
+                        double *loss, void *stream);
+
+/* Gradient-descent step w <- w - lr g with caller-supplied gradients
+ * (Sec. 2.2, no momentum). */
+mlp_status mlp_update(mlp_t net, const void *gW1, const void *gb1,
+                      const void *gw2, const void *gb2, void *stream);
+
+/* One training step by the plain path: separate forward, output, gradient,
+ * reduction and update kernels with the hidden activations materialised in
+ * device memory.  Same result as one full-batch epoch of mlp_train_epochs. */
+mlp_status mlp_step_plain(mlp_t net, const void *X, const void *y, int64_t n,
+                          double *loss, void *stream);
+
+/* Train `epochs` epochs (Sec. 2.2, Fig. 2).  minibatch <= 0 or >= n is full-batch
+ * gradient descent (one update per epoch); otherwise each epoch visits
+ * contiguous slices of `minibatch` rows in order with one update per slice
+ * (the last slice may be shorter; minibatch = 1 is online backpropagation).
+ * loss_hist [epochs] (device, may be NULL) receives (C/2) sum_i (o_i - y_i)^2
+ * with o_i taken when row i was visited (C = 1/n or 1), accumulated in FP64;
+ * gnorm_hist [epochs] (device, may be NULL) the FP64 2-norm of the last
+ * update's gradient.  Small networks run as one fused cooperative kernel per
+ * call (forward, backward, cross-block reduction and update per step); larger
+ * ones fall back to the plain path per step. */
+mlp_status mlp_train_epochs(mlp_t net, const void *X, const void *y, int64_t n,
+                            int32_t epochs, int64_t minibatch, double *loss_hist,
+                            double *gnorm_hist, void *stream);
+
+/* mlp_train_epochs on host buffers: copies X and y to device staging memory
+ * owned by the handle, trains, and copies the loss history back to
+ * loss_hist_host (may be NULL).  Synchronous. */
+mlp_status mlp_train_host(mlp_t net, const void *X_host, const void *y_host,
+                          int64_t n, int32_t epochs, int64_t minibatch,
+                          double *loss_hist_host, void *stream);
+
+/* Classification (Sec. 2.2): labels[i] = 1 iff o_i >= 0.5, else 0. */
+mlp_status mlp_predict(mlp_t net, const void *X, int64_t n, int8_t *labels, void *stream);
+
+/* Synchronise `stream`, then return and clear the handle's device status:
+ * MLP_OK, MLP_ETIMEOUT or MLP_ENONFINITE. */
+mlp_status mlp_check(mlp_t net, void *stream);
+
+/*
+ * Handle-free forms on caller-owned weights, for automatic differentiation
+ * frameworks.  prec is MLP_FP32 or MLP_FP64 (all of X, weights, hid, o, dLdo
+ * and gradients are then float or double).  Both need a caller-owned device
+ * workspace of at least mlp_workspace_bytes(prec, D, H, n) bytes (256-byte
+ * aligned); it is scratch for the duration of the call only, so calls that
+ * may overlap on the GPU need separate workspaces.
+ *   mlp_forward_w: writes hid [n x H] (if not NULL) and o [n].
+ *   mlp_backward_w: backpropagates an arbitrary upstream gradient dLdo [n]
+ *     (Sec. 2.2 chain rule) using the saved hid [n x H] and o [n]; writes gW1,
+ *     gb1, gw2, gb2 and, if gX != NULL, gX [n x D] = d1 W1.
+ */
+mlp_status mlp_workspace_bytes(int32_t prec, int32_t D, int32_t H, int64_t n, uint64_t *bytes);
+mlp_status mlp_forward_w(int32_t prec, int32_t act, int32_t D, int32_t H, int64_t n,
+                         const void *X, const void *W1, const void *b1,
+                         const void *w2, const void *b2, void *hid, void *o,
+                         void *workspace, uint64_t workspace_bytes, void *stream);
+mlp_status mlp_backward_w(int32_t prec, int32_t act, int32_t D, int32_t H, int64_t n,
+                          const void *X, const void *W1, const void *w2,
+                          const void *hid, const void *o, const void *dLdo,
+                          void *gW1, void *gb1, void *gw2, void *gb2, void *gX,
+                          void *workspace, uint64_t workspace_bytes, void *stream);
+
+/* Test hook for the failure path of cross-block waits: when skip_block >= 0,
+ * that block of the next fused training launches returns before its first
+ * barrier, so the other blocks give up after about one second and the launch
+ * records MLP_ETIMEOUT (read it with mlp_check).  -1 restores normal runs. */
+mlp_status mlp_debug_skip_block(mlp_t net, int32_t skip_block);
+
+/* Rows per block of the fused training kernel (tuning knob, default 64). */
+mlp_status mlp_set_rows_per_block(mlp_t net, int32_t rows);
+
+/*
+ * Many independent networks trained in one launch (the paper trains its male
+ * and female subsets as separate networks, Sec. 2.1; here any number, each with
+ * its own H and n).  Every field is read on the host; X, y, params and
+ * loss_hist point to device memory.  params holds the net's packed weights
+ * [W1 (H x D), b1, w2, b2] (float), trained in place; loss_hist [epochs] may be
+ * NULL.  All nets share D, epochs, lr, loss_mean and full-batch updates.
+ */
+typedef struct {
+    int32_t H;
+    int64_t n;
+    const void *X;
+    const float *y;
+    float *params;
+    double *loss_hist;
+} mlp_net_desc;
+
+mlp_status mlp_batch_train(int32_t prec, int32_t act, int32_t D,
+                           const mlp_net_desc *nets, int32_t n_nets,
+                           int32_t epochs, float lr, int32_t loss_mean,
+                           void *stream);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char *mlp_last_error(void);
+
+/* Library version string. */
+const char *mlp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MLP_GB300_H */

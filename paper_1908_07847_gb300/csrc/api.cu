@@ -1,0 +1,477 @@
+// C ABI of the training library (declarations and contracts in mlp_gb300.h).
+// Host code only: argument checks, handle-owned memory, kernel dispatch.
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "mlp_internal.cuh"
+
+struct mlp_net {
+    mlp_config cfg;
+    int device;
+    int sms;
+    size_t esz;       // bytes per master weight (4 or 8)
+    int64_t P;        // (D + 2) H + 1
+    void *params;     // packed master weights [W1, b1, w2, b2]
+    void *grads;      // packed gradients
+    int *status;      // device status word
+    double *dtmp;     // 64 doubles of reduction scratch + 1 step loss
+    void *pw = nullptr;   // plain workspace
+    size_t pw_cap = 0;
+    void *hid = nullptr;  // n x H activations (plain path)
+    size_t hid_cap = 0;
+    void *obuf = nullptr; // n outputs
+    size_t obuf_cap = 0;
+    void *fs = nullptr;   // fused-kernel scratch
+    size_t fs_cap = 0;
+    void *xstage = nullptr, *ystage = nullptr;  // mlp_train_host staging
+    size_t xstage_cap = 0, ystage_cap = 0;
+    double *lstage = nullptr;
+    size_t lstage_cap = 0;
+    int skip_block = -1;
+    int rows_per_block = 64;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+mlp_status fail(mlp_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+mlp_status cuda_fail(cudaError_t e, const char *where) {
+    if (e == cudaErrorMemoryAllocation)
+        return fail(MLP_ENOMEM, "%s: %s", where, cudaGetErrorString(e));
+    return fail(MLP_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define CK(call, where)                                   \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return cuda_fail(e_, where); \
+    } while (0)
+
+// Makes the handle's device current for the scope of a call, then restores.
+struct DeviceScope {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceScope(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; return; }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceScope() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+mlp_status grow(void **p, size_t *cap, size_t need, const char *what) {
+    if (need <= *cap && *p) return MLP_OK;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    size_t want = need < 256 ? 256 : need;
+    cudaError_t e = cudaMalloc(p, want);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return fail(MLP_ENOMEM, "cannot allocate %zu bytes for %s", want, what);
+    }
+    *cap = want;
+    return MLP_OK;
+}
+
+size_t x_elem_bytes(int prec) { return prec == MLP_FP64 ? 8 : (prec == MLP_BF16 ? 2 : 4); }
+
+char *W1p(mlp_t h) { return (char *)h->params; }
+char *b1p(mlp_t h) { return (char *)h->params + h->esz * (size_t)h->cfg.H * h->cfg.D; }
+char *w2p(mlp_t h) { return b1p(h) + h->esz * (size_t)h->cfg.H; }
+char *b2p(mlp_t h) { return w2p(h) + h->esz * (size_t)h->cfg.H; }
+char *gW1p(mlp_t h) { return (char *)h->grads; }
+char *gb1p(mlp_t h) { return (char *)h->grads + h->esz * (size_t)h->cfg.H * h->cfg.D; }
+char *gw2p(mlp_t h) { return gb1p(h) + h->esz * (size_t)h->cfg.H; }
+char *gb2p(mlp_t h) { return gw2p(h) + h->esz * (size_t)h->cfg.H; }
+
+mlp_status ensure_plain(mlp_t h, int64_t n, bool need_hid, mlp::PlainWork *w) {
+    const int prec = h->cfg.prec, D = h->cfg.D, H = h->cfg.H;
+    mlp_status s = grow(&h->pw, &h->pw_cap, mlp::plain_workspace_bytes(prec, D, H, n, h->sms), "workspace");
+    if (s) return s;
+    mlp::plain_workspace_carve(h->pw, prec, D, H, n, h->sms, w);
+    s = grow(&h->obuf, &h->obuf_cap, h->esz * (size_t)(n > 0 ? n : 1), "outputs");
+    if (s) return s;
+    if (need_hid) {
+        s = grow(&h->hid, &h->hid_cap, h->esz * (size_t)(n > 0 ? n : 1) * (size_t)H, "activations");
+        if (s) return s;
+    }
+    return MLP_OK;
+}
+
+double loss_scale(int loss_mean, int64_t n) { return loss_mean ? (n > 0 ? 1.0 / (double)n : 0.0) : 1.0; }
+
+// One plain-path gradient evaluation into the handle's packed gradient buffer
+// (or caller pointers); loss (may be NULL) = 0.5 * c_loss * sse.
+mlp_status plain_grad(mlp_t h, const void *X, const void *y, int64_t n, void *gW1, void *gb1, void *gw2,
+                      void *gb2, double *loss, double c_loss, cudaStream_t st) {
+    mlp::PlainWork w;
+    mlp_status s = ensure_plain(h, n, true, &w);
+    if (s) return s;
+    const double c = loss_scale(h->cfg.loss_mean, n);
+    CK(mlp::plain_forward(h->cfg.prec, h->cfg.act, h->cfg.D, h->cfg.H, n, X, W1p(h), b1p(h), w2p(h), b2p(h),
+                          h->hid, h->obuf, y, nullptr, c, w, st),
+       "forward kernels");
+    CK(mlp::plain_backward(h->cfg.prec, h->cfg.act, h->cfg.D, h->cfg.H, n, X, W1p(h), w2p(h), h->hid, gW1, gb1,
+                           gw2, gb2, nullptr, loss, c_loss, h->status, w, st),
+       "backward kernels");
+    return MLP_OK;
+}
+
+mlp_status check_handle(mlp_t h) {
+    if (!h) return fail(MLP_EINVAL, "null handle");
+    return MLP_OK;
+}
+
+}  // namespace
+
+namespace mlp {
+int device_sm_count() {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
+    return n > 0 ? n : 1;
+}
+}  // namespace mlp
+
+extern "C" {
+
+const char *mlp_last_error(void) { return g_err.c_str(); }
+
+const char *mlp_version(void) { return "mlp_gb300 1.0 (sm_103a)"; }
+
+mlp_status mlp_create(const mlp_config *cfg, mlp_t *out) {
+    if (!cfg || !out) return fail(MLP_EINVAL, "mlp_create: null argument");
+    *out = nullptr;
+    if (cfg->D < 1 || cfg->D > 4096) return fail(MLP_EINVAL, "mlp_create: D=%d out of 1..4096", cfg->D);
+    if (cfg->H < 1 || cfg->H > 65536) return fail(MLP_EINVAL, "mlp_create: H=%d out of 1..65536", cfg->H);
+    if (cfg->prec < MLP_FP32 || cfg->prec > MLP_FP64) return fail(MLP_EINVAL, "mlp_create: bad precision");
+    if (cfg->act != MLP_ACT_SIGMOID && cfg->act != MLP_ACT_TANH) return fail(MLP_EINVAL, "mlp_create: bad act");
+    if (!(cfg->lr == cfg->lr)) return fail(MLP_EINVAL, "mlp_create: lr is NaN");
+    mlp_t h = new (std::nothrow) mlp_net();
+    if (!h) return fail(MLP_ENOMEM, "mlp_create: host allocation");
+    h->cfg = *cfg;
+    h->cfg.loss_mean = cfg->loss_mean ? 1 : 0;
+    if (cudaGetDevice(&h->device) != cudaSuccess) {
+        delete h;
+        return fail(MLP_ECUDA, "mlp_create: no CUDA device");
+    }
+    h->sms = mlp::device_sm_count();
+    h->esz = cfg->prec == MLP_FP64 ? 8 : 4;
+    h->P = (int64_t)(cfg->D + 2) * cfg->H + 1;
+    size_t pb = h->esz * (size_t)h->P;
+    size_t need = 2 * ((pb + 255) & ~(size_t)255) + 256 + 66 * sizeof(double);
+    char *base = nullptr;
+    if (cudaMalloc((void **)&base, need) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return fail(MLP_ENOMEM, "mlp_create: cannot allocate %zu bytes", need);
+    }
+    h->params = base;
+    h->grads = base + ((pb + 255) & ~(size_t)255);
+    h->status = (int *)(base + 2 * ((pb + 255) & ~(size_t)255));
+    h->dtmp = (double *)((char *)h->status + 256);
+    if (cudaMemset(base, 0, need) != cudaSuccess) {
+        cudaFree(base);
+        delete h;
+        return fail(MLP_ECUDA, "mlp_create: memset failed");
+    }
+    *out = h;
+    return MLP_OK;
+}
+
+void mlp_destroy(mlp_t h) {
+    if (!h) return;
+    DeviceScope ds(h->device);
+    cudaFree(h->params);
+    if (h->pw) cudaFree(h->pw);
+    if (h->hid) cudaFree(h->hid);
+    if (h->obuf) cudaFree(h->obuf);
+    if (h->fs) cudaFree(h->fs);
+    if (h->xstage) cudaFree(h->xstage);
+    if (h->ystage) cudaFree(h->ystage);
+    if (h->lstage) cudaFree(h->lstage);
+    delete h;
+}
+
+mlp_status mlp_set_weights(mlp_t h, const void *W1, const void *b1, const void *w2, const void *b2) {
+    if (check_handle(h)) return MLP_EINVAL;
+    if (!W1 || !b1 || !w2 || !b2) return fail(MLP_EINVAL, "mlp_set_weights: null pointer");
+    DeviceScope ds(h->device);
+    const size_t HD = (size_t)h->cfg.H * h->cfg.D, Hs = (size_t)h->cfg.H;
+    CK(cudaMemcpy(W1p(h), W1, h->esz * HD, cudaMemcpyHostToDevice), "mlp_set_weights");
+    CK(cudaMemcpy(b1p(h), b1, h->esz * Hs, cudaMemcpyHostToDevice), "mlp_set_weights");
+    CK(cudaMemcpy(w2p(h), w2, h->esz * Hs, cudaMemcpyHostToDevice), "mlp_set_weights");
+    CK(cudaMemcpy(b2p(h), b2, h->esz, cudaMemcpyHostToDevice), "mlp_set_weights");
+    return MLP_OK;
+}
+
+mlp_status mlp_get_weights(mlp_t h, void *W1, void *b1, void *w2, void *b2) {
+    if (check_handle(h)) return MLP_EINVAL;
+    if (!W1 || !b1 || !w2 || !b2) return fail(MLP_EINVAL, "mlp_get_weights: null pointer");
+    DeviceScope ds(h->device);
+    const size_t HD = (size_t)h->cfg.H * h->cfg.D, Hs = (size_t)h->cfg.H;
+    CK(cudaDeviceSynchronize(), "mlp_get_weights");
+    CK(cudaMemcpy(W1, W1p(h), h->esz * HD, cudaMemcpyDeviceToHost), "mlp_get_weights");
+    CK(cudaMemcpy(b1, b1p(h), h->esz * Hs, cudaMemcpyDeviceToHost), "mlp_get_weights");
+    CK(cudaMemcpy(w2, w2p(h), h->esz * Hs, cudaMemcpyDeviceToHost), "mlp_get_weights");
+    CK(cudaMemcpy(b2, b2p(h), h->esz, cudaMemcpyDeviceToHost), "mlp_get_weights");
+    return MLP_OK;
+}
+
+mlp_status mlp_weights_device(mlp_t h, void **p) {
+    if (check_handle(h)) return MLP_EINVAL;
+    if (!p) return fail(MLP_EINVAL, "mlp_weights_device: null pointer");
+    *p = h->params;
+    return MLP_OK;
+}
+
+mlp_status mlp_forward(mlp_t h, const void *X, int64_t n, void *o, void *stream) {
+    if (check_handle(h)) return MLP_EINVAL;
+    if (n < 0 || (n > 0 && (!X || !o))) return fail(MLP_EINVAL, "mlp_forward: bad arguments");
+    if (n == 0) return MLP_OK;
+    DeviceScope ds(h->device);
+    mlp::PlainWork w;
+    mlp_status s = ensure_plain(h, n, false, &w);
+    if (s) return s;
+    CK(mlp::plain_forward(h->cfg.prec, h->cfg.act, h->cfg.D, h->cfg.H, n, X, W1p(h), b1p(h), w2p(h), b2p(h),
+                          nullptr, o, nullptr, nullptr, 0.0, w, (cudaStream_t)stream),
+       "mlp_forward");
+    return MLP_OK;
+}
+
+mlp_status mlp_backward(mlp_t h, const void *X, const void *y, int64_t n, void *gW1, void *gb1, void *gw2,
+                        void *gb2, double *loss, void *stream) {
+    if (check_handle(h)) return MLP_EINVAL;
+    if (n < 0 || !gW1 || !gb1 || !gw2 || !gb2 || (n > 0 && (!X || !y)))
+        return fail(MLP_EINVAL, "mlp_backward: bad arguments");
+    DeviceScope ds(h->device);
+    return plain_grad(h, X, y, n, gW1, gb1, gw2, gb2, loss, loss_scale(h->cfg.loss_mean, n),
+                      (cudaStream_t)stream);
+}
+
+mlp_status mlp_update(mlp_t h, const void *gW1, const void *gb1, const void *gw2, const void *gb2,
+                      void *stream) {
+    if (check_handle(h)) return MLP_EINVAL;
+    if (!gW1 || !gb1 || !gw2 || !gb2) return fail(MLP_EINVAL, "mlp_update: null gradient");
+    DeviceScope ds(h->device);
+    CK(mlp::plain_update(h->cfg.prec, h->cfg.D, h->cfg.H, (double)h->cfg.lr, W1p(h), b1p(h), w2p(h), b2p(h), gW1,
+                         gb1, gw2, gb2, (cudaStream_t)stream),
+       "mlp_update");
+    return MLP_OK;
+}
+
+mlp_status mlp_step_plain(mlp_t h, const void *X, const void *y, int64_t n, double *loss, void *stream) {
+    if (check_handle(h)) return MLP_EINVAL;
+    if (n < 0 || (n > 0 && (!X || !y))) return fail(MLP_EINVAL, "mlp_step_plain: bad arguments");
+    DeviceScope ds(h->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    mlp_status s = plain_grad(h, X, y, n, gW1p(h), gb1p(h), gw2p(h), gb2p(h), loss,
+                              loss_scale(h->cfg.loss_mean, n), st);
+    if (s) return s;
+    CK(mlp::plain_update(h->cfg.prec, h->cfg.D, h->cfg.H, (double)h->cfg.lr, W1p(h), b1p(h), w2p(h), b2p(h),
+                         gW1p(h), gb1p(h), gw2p(h), gb2p(h), st),
+       "mlp_step_plain update");
+    return MLP_OK;
+}
+
+mlp_status mlp_train_epochs(mlp_t h, const void *X, const void *y, int64_t n, int32_t epochs, int64_t minibatch,
+                            double *loss_hist, double *gnorm_hist, void *stream) {
+    if (check_handle(h)) return MLP_EINVAL;
+    if (n < 0 || epochs < 0 || (n > 0 && (!X || !y))) return fail(MLP_EINVAL, "mlp_train_epochs: bad arguments");
+    if (epochs == 0) return MLP_OK;
+    DeviceScope ds(h->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n == 0) {
+        if (loss_hist) CK(cudaMemsetAsync(loss_hist, 0, sizeof(double) * epochs, st), "mlp_train_epochs");
+        if (gnorm_hist) CK(cudaMemsetAsync(gnorm_hist, 0, sizeof(double) * epochs, st), "mlp_train_epochs");
+        return MLP_OK;
+    }
+    const int D = h->cfg.D, H = h->cfg.H;
+    if (h->cfg.prec == MLP_FP32 && mlp::fused_supported(D, H)) {
+        mlp_status s = grow(&h->fs, &h->fs_cap, mlp::fused_scratch_bytes(D, H, h->sms), "fused scratch");
+        if (s) return s;
+        mlp::FusedScratch fsc;
+        mlp::fused_scratch_carve(h->fs, D, H, h->sms, &fsc);
+        CK(mlp::fused_train(h->cfg.act, D, H, n, (const float *)X, (const float *)y, (float *)h->params,
+                            h->cfg.lr, h->cfg.loss_mean, epochs, minibatch, loss_hist, gnorm_hist, h->status,
+                            fsc, h->rows_per_block, h->skip_block, st, nullptr),
+           "fused training kernel");
+        return MLP_OK;
+    }
+    // Plain path, one step at a time.
+    const int64_t mbs = (minibatch <= 0 || minibatch >= n) ? n : minibatch;
+    const double C = loss_scale(h->cfg.loss_mean, n);
+    const size_t xb = x_elem_bytes(h->cfg.prec) * (size_t)D;
+    for (int e = 0; e < epochs; ++e) {
+        int first = 1;
+        for (int64_t b0 = 0; b0 < n; b0 += mbs) {
+            const int64_t m = (n - b0) < mbs ? (n - b0) : mbs;
+            mlp_status s = plain_grad(h, (const char *)X + xb * b0, (const char *)y + h->esz * b0, m, gW1p(h),
+                                      gb1p(h), gw2p(h), gb2p(h), h->dtmp + 64, C, st);
+            if (s) return s;
+            if (gnorm_hist && b0 + mbs >= n)
+                CK(mlp::plain_gnorm(h->cfg.prec, h->P, h->grads, h->dtmp, gnorm_hist + e, st), "gnorm");
+            CK(mlp::plain_update(h->cfg.prec, D, H, (double)h->cfg.lr, W1p(h), b1p(h), w2p(h), b2p(h), gW1p(h),
+                                 gb1p(h), gw2p(h), gb2p(h), st),
+               "update");
+            if (loss_hist) CK(mlp::plain_accum(loss_hist + e, h->dtmp + 64, first, st), "loss");
+            first = 0;
+        }
+    }
+    return MLP_OK;
+}
+
+mlp_status mlp_train_host(mlp_t h, const void *X_host, const void *y_host, int64_t n, int32_t epochs,
+                          int64_t minibatch, double *loss_hist_host, void *stream) {
+    if (check_handle(h)) return MLP_EINVAL;
+    if (n < 0 || epochs < 0 || (n > 0 && (!X_host || !y_host)))
+        return fail(MLP_EINVAL, "mlp_train_host: bad arguments");
+    DeviceScope ds(h->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t xb = x_elem_bytes(h->cfg.prec) * (size_t)h->cfg.D * (size_t)n;
+    const size_t yb = h->esz * (size_t)n;
+    mlp_status s = grow(&h->xstage, &h->xstage_cap, xb, "X staging");
+    if (s) return s;
+    s = grow(&h->ystage, &h->ystage_cap, yb, "y staging");
+    if (s) return s;
+    s = grow((void **)&h->lstage, &h->lstage_cap, sizeof(double) * (size_t)(epochs > 0 ? epochs : 1), "loss staging");
+    if (s) return s;
+    if (n > 0) {
+        CK(cudaMemcpyAsync(h->xstage, X_host, xb, cudaMemcpyHostToDevice, st), "mlp_train_host copy X");
+        CK(cudaMemcpyAsync(h->ystage, y_host, yb, cudaMemcpyHostToDevice, st), "mlp_train_host copy y");
+    }
+    s = mlp_train_epochs(h, h->xstage, h->ystage, n, epochs, minibatch, h->lstage, nullptr, stream);
+    if (s) return s;
+    if (loss_hist_host && epochs > 0)
+        CK(cudaMemcpyAsync(loss_hist_host, h->lstage, sizeof(double) * epochs, cudaMemcpyDeviceToHost, st),
+           "mlp_train_host copy loss");
+    CK(cudaStreamSynchronize(st), "mlp_train_host sync");
+    return MLP_OK;
+}
+
+mlp_status mlp_predict(mlp_t h, const void *X, int64_t n, int8_t *labels, void *stream) {
+    if (check_handle(h)) return MLP_EINVAL;
+    if (n < 0 || (n > 0 && (!X || !labels))) return fail(MLP_EINVAL, "mlp_predict: bad arguments");
+    if (n == 0) return MLP_OK;
+    DeviceScope ds(h->device);
+    mlp::PlainWork w;
+    mlp_status s = ensure_plain(h, n, false, &w);
+    if (s) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(mlp::plain_forward(h->cfg.prec, h->cfg.act, h->cfg.D, h->cfg.H, n, X, W1p(h), b1p(h), w2p(h), b2p(h),
+                          nullptr, h->obuf, nullptr, nullptr, 0.0, w, st),
+       "mlp_predict forward");
+    CK(mlp::plain_labels(h->cfg.prec, n, h->obuf, labels, st), "mlp_predict labels");
+    return MLP_OK;
+}
+
+mlp_status mlp_check(mlp_t h, void *stream) {
+    if (check_handle(h)) return MLP_EINVAL;
+    DeviceScope ds(h->device);
+    CK(cudaStreamSynchronize((cudaStream_t)stream), "mlp_check sync");
+    int st = 0;
+    CK(cudaMemcpy(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost), "mlp_check read");
+    CK(cudaMemset(h->status, 0, sizeof(int)), "mlp_check clear");
+    if (st & mlp::ST_TIMEOUT) return fail(MLP_ETIMEOUT, "a cross-block wait gave up");
+    if (st & mlp::ST_NONFINITE) return fail(MLP_ENONFINITE, "a loss was not finite");
+    return MLP_OK;
+}
+
+mlp_status mlp_debug_skip_block(mlp_t h, int32_t skip_block) {
+    if (check_handle(h)) return MLP_EINVAL;
+    h->skip_block = skip_block < 0 ? -1 : skip_block;
+    return MLP_OK;
+}
+
+mlp_status mlp_set_rows_per_block(mlp_t h, int32_t rows) {
+    if (check_handle(h)) return MLP_EINVAL;
+    if (rows < 1) return fail(MLP_EINVAL, "mlp_set_rows_per_block: rows must be >= 1");
+    h->rows_per_block = rows;
+    return MLP_OK;
+}
+
+mlp_status mlp_workspace_bytes(int32_t prec, int32_t D, int32_t H, int64_t n, uint64_t *bytes) {
+    if (!bytes || D < 1 || H < 1 || n < 0 || prec < MLP_FP32 || prec > MLP_FP64)
+        return fail(MLP_EINVAL, "mlp_workspace_bytes: bad arguments");
+    *bytes = mlp::plain_workspace_bytes(prec, D, H, n, mlp::device_sm_count());
+    return MLP_OK;
+}
+
+static mlp_status check_w(const char *fn, int32_t prec, int32_t act, int32_t D, int32_t H, int64_t n,
+                          uint64_t ws_bytes, const void *ws) {
+    if (prec != MLP_FP32 && prec != MLP_FP64) return fail(MLP_EINVAL, "%s: prec must be FP32 or FP64", fn);
+    if (act != MLP_ACT_SIGMOID && act != MLP_ACT_TANH) return fail(MLP_EINVAL, "%s: bad act", fn);
+    if (D < 1 || H < 1 || n < 0) return fail(MLP_EINVAL, "%s: bad shape", fn);
+    uint64_t need = mlp::plain_workspace_bytes(prec, D, H, n, mlp::device_sm_count());
+    if (n > 0 && (!ws || ws_bytes < need))
+        return fail(MLP_EINVAL, "%s: workspace of %llu bytes needed", fn, (unsigned long long)need);
+    if (((uintptr_t)ws & 255) != 0) return fail(MLP_EINVAL, "%s: workspace not 256-byte aligned", fn);
+    return MLP_OK;
+}
+
+mlp_status mlp_forward_w(int32_t prec, int32_t act, int32_t D, int32_t H, int64_t n, const void *X,
+                         const void *W1, const void *b1, const void *w2, const void *b2, void *hid, void *o,
+                         void *workspace, uint64_t workspace_bytes, void *stream) {
+    mlp_status s = check_w("mlp_forward_w", prec, act, D, H, n, workspace_bytes, workspace);
+    if (s) return s;
+    if (n > 0 && (!X || !W1 || !b1 || !w2 || !b2 || !o)) return fail(MLP_EINVAL, "mlp_forward_w: null pointer");
+    if (n == 0) return MLP_OK;
+    mlp::PlainWork w;
+    mlp::plain_workspace_carve(workspace, prec, D, H, n, mlp::device_sm_count(), &w);
+    CK(mlp::plain_forward(prec, act, D, H, n, X, W1, b1, w2, b2, hid, o, nullptr, nullptr, 0.0, w,
+                          (cudaStream_t)stream),
+       "mlp_forward_w");
+    return MLP_OK;
+}
+
+mlp_status mlp_backward_w(int32_t prec, int32_t act, int32_t D, int32_t H, int64_t n, const void *X,
+                          const void *W1, const void *w2, const void *hid, const void *o, const void *dLdo,
+                          void *gW1, void *gb1, void *gw2, void *gb2, void *gX, void *workspace,
+                          uint64_t workspace_bytes, void *stream) {
+    mlp_status s = check_w("mlp_backward_w", prec, act, D, H, n, workspace_bytes, workspace);
+    if (s) return s;
+    if (!gW1 || !gb1 || !gw2 || !gb2 || (n > 0 && (!X || !W1 || !w2 || !hid || !o || !dLdo)))
+        return fail(MLP_EINVAL, "mlp_backward_w: null pointer");
+    mlp::PlainWork w;
+    mlp::plain_workspace_carve(workspace, prec, D, H, n, mlp::device_sm_count(), &w);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n > 0) CK(mlp::plain_d2_upstream(prec, n, o, dLdo, w.d2, st), "mlp_backward_w d2");
+    CK(mlp::plain_backward(prec, act, D, H, n, X, W1, w2, hid, gW1, gb1, gw2, gb2, gX, nullptr, 0.0, nullptr, w,
+                           st),
+       "mlp_backward_w");
+    return MLP_OK;
+}
+
+mlp_status mlp_batch_train(int32_t prec, int32_t act, int32_t D, const mlp_net_desc *nets, int32_t n_nets,
+                           int32_t epochs, float lr, int32_t loss_mean, void *stream) {
+    (void)prec;
+    (void)act;
+    (void)D;
+    (void)nets;
+    (void)n_nets;
+    (void)epochs;
+    (void)lr;
+    (void)loss_mean;
+    (void)stream;
+    return fail(MLP_EUNSUPPORTED, "mlp_batch_train: not built yet");
+}
+
+}  // extern "C"

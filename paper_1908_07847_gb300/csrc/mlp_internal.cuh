@@ -1,0 +1,183 @@
+// Internal declarations shared by the library's translation units.
+// The method: one-hidden-layer feed-forward network, sigmoid (Eq. 1) or tanh
+// hidden units, sigmoid output, squared-error backpropagation and gradient
+// descent without momentum (Sec. 2.2 of arXiv 1908.07847).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mlp_gb300.h"
+
+namespace mlp {
+
+// Device status bits (mlp_net::status).
+constexpr int ST_TIMEOUT = 1;
+constexpr int ST_NONFINITE = 2;
+
+// A cross-block wait gives up after this many nanoseconds.
+constexpr unsigned long long WAIT_LIMIT_NS = 1000000000ull;
+
+// ---------------------------------------------------------------- activations
+
+template <int ACT> struct Act;
+
+// Eq. 1 sigmoid; derivative through the value: s (1 - s).
+template <> struct Act<MLP_ACT_SIGMOID> {
+    static __device__ __forceinline__ float f(float x) { return 1.0f / (1.0f + expf(-x)); }
+    static __device__ __forceinline__ double f(double x) { return 1.0 / (1.0 + exp(-x)); }
+    static __device__ __forceinline__ float df(float v) { return v * (1.0f - v); }
+    static __device__ __forceinline__ double df(double v) { return v * (1.0 - v); }
+};
+
+// tanh (Sec. 2.2 names it as the other traditional activation); 1 - t^2.
+template <> struct Act<MLP_ACT_TANH> {
+    static __device__ __forceinline__ float f(float x) { return tanhf(x); }
+    static __device__ __forceinline__ double f(double x) { return tanh(x); }
+    static __device__ __forceinline__ float df(float v) { return 1.0f - v * v; }
+    static __device__ __forceinline__ double df(double v) { return 1.0 - v * v; }
+};
+
+__device__ __forceinline__ float sigmoid_out(float x) { return 1.0f / (1.0f + expf(-x)); }
+__device__ __forceinline__ double sigmoid_out(double x) { return 1.0 / (1.0 + exp(-x)); }
+
+// ------------------------------------------------------------- element loads
+
+// X element as the arithmetic type T: float from float, float from bf16 bits,
+// double from double.
+template <typename T, typename TX> __device__ __forceinline__ T ldx(const TX *p, int64_t i);
+template <> __device__ __forceinline__ float ldx<float, float>(const float *p, int64_t i) { return p[i]; }
+template <> __device__ __forceinline__ double ldx<double, double>(const double *p, int64_t i) { return p[i]; }
+template <> __device__ __forceinline__ float ldx<float, uint16_t>(const uint16_t *p, int64_t i) {
+    return __uint_as_float(((uint32_t)p[i]) << 16);
+}
+
+// ------------------------------------------------------------------- helpers
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int ld_volatile(const int *p) {
+    return *(const volatile int *)p;
+}
+
+template <typename T> __device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+// Grid-wide barrier for kernels launched cooperatively (all blocks resident).
+// `bar` counts arrivals monotonically from 0 (the host zeroes it before the
+// launch); the k-th barrier of the launch waits until it reaches k * nblocks.
+// The wait gives up after WAIT_LIMIT_NS, or as soon as another block has
+// recorded a failure, and then returns false after recording ST_TIMEOUT.
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned target, int *status) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(bar, 1u);
+        unsigned long long t0 = global_ns();
+        int ok = 1;
+        while (ld_acquire(bar) < target) {
+            if (ld_volatile(status) & ST_TIMEOUT) { ok = 0; break; }
+            if (global_ns() - t0 > WAIT_LIMIT_NS) {
+                atomicOr(status, ST_TIMEOUT);
+                ok = 0;
+                break;
+            }
+            __nanosleep(32);
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// ------------------------------------------------------ plain-path launchers
+// Generic kernels for any D and H (FP32, FP64; BF16 inputs with FP32 math).
+// All return cudaGetLastError() of their launches.
+
+struct PlainWork {
+    // device scratch, sized by plain_workspace_bytes()
+    void *z2part;   // [ceil(H/64)] x n   (T)
+    void *d2;       // n                   (T)
+    double *ssep;   // ceil(n/256)
+    void *part;     // C x P               (T)
+    int C;          // number of sample chunks for gradient partials
+    int64_t CH;     // rows per chunk
+};
+
+size_t plain_workspace_bytes(int prec, int D, int H, int64_t n, int sms);
+void plain_workspace_carve(void *base, int prec, int D, int H, int64_t n, int sms, PlainWork *w);
+
+// hid may be NULL.  When y != NULL also writes d2 = c (o - y) o (1 - o) and the
+// per-block squared-error partials; when dLdo != NULL writes d2 = dLdo o (1-o).
+cudaError_t plain_forward(int prec, int act, int D, int H, int64_t n, const void *X,
+                          const void *W1, const void *b1, const void *w2, const void *b2,
+                          void *hid, void *o, const void *y, const void *dLdo, double c,
+                          const PlainWork &w, cudaStream_t st);
+
+// Gradient partials and their fixed-order reduction into gW1, gb1, gw2, gb2.
+// Needs hid and d2 from plain_forward.  loss (may be NULL) = 0.5 c_loss sse.
+// gX (may be NULL) = d1 W1.
+cudaError_t plain_backward(int prec, int act, int D, int H, int64_t n, const void *X,
+                           const void *W1, const void *w2, const void *hid,
+                           void *gW1, void *gb1, void *gw2, void *gb2, void *gX,
+                           double *loss, double c_loss, int *status,
+                           const PlainWork &w, cudaStream_t st);
+
+// w <- w - lr g over the four parameter arrays.
+cudaError_t plain_update(int prec, int D, int H, double lr, void *W1, void *b1, void *w2,
+                         void *b2, const void *gW1, const void *gb1, const void *gw2,
+                         const void *gb2, cudaStream_t st);
+
+// ||g||_2 in FP64 (fixed order) written to *out; scratch64 holds 64 doubles.
+cudaError_t plain_gnorm(int prec, int64_t P, const void *g_packed, double *scratch64, double *out,
+                        cudaStream_t st);
+
+// d2 = dLdo o (1 - o) into w.d2 (autograd backward).
+cudaError_t plain_d2_upstream(int prec, int64_t n, const void *o, const void *dLdo, void *d2, cudaStream_t st);
+
+// *dst = (first ? 0 : *dst) + *src (one thread).
+cudaError_t plain_accum(double *dst, const double *src, int first, cudaStream_t st);
+
+// labels[i] = o_i >= 0.5
+cudaError_t plain_labels(int prec, int64_t n, const void *o, int8_t *labels, cudaStream_t st);
+
+// ------------------------------------------------------- fused-path launcher
+
+struct FusedScratch {
+    float *part;     // G x P
+    double *lossp;   // G
+    double *gnp;     // G
+    unsigned *bar;   // 1
+};
+
+// True if the fused cooperative kernel supports this shape.
+bool fused_supported(int D, int H);
+// Scratch bytes for the fused kernel at its largest grid.
+size_t fused_scratch_bytes(int D, int H, int sms);
+void fused_scratch_carve(void *base, int D, int H, int sms, FusedScratch *s);
+
+// Trains in place on the packed FP32 params [W1, b1, w2, b2].
+cudaError_t fused_train(int act, int D, int H, int64_t n, const float *X, const float *y,
+                        float *params, float lr, int loss_mean, int epochs, int64_t mb,
+                        double *loss_hist, double *gnorm_hist, int *status,
+                        const FusedScratch &s, int rows_per_block, int skip_block,
+                        cudaStream_t st, int *grid_used);
+
+int device_sm_count();
+
+}  // namespace mlp
