@@ -2,18 +2,23 @@
 // launch runs every step of every epoch.  Per step (Sec. 2.2 of arXiv
 // 1908.07847: feed-forward, output error, backpropagation, gradient descent
 // with no momentum):
-//   1. every block stages its rows of X in shared memory; each warp takes a
-//      row at a time, each lane owns up to two hidden neurons (the paper's
-//      "each neuron on its own thread") with their incoming weights in
-//      registers, computes z1, h, the warp-shuffle sum z2, o (Eq. 1), the
-//      output delta and the hidden deltas, and accumulates the neuron's
-//      gradient row in registers; activations never leave the chip;
+//   1. every block stages the weights and its rows of X in shared memory with
+//      asynchronous copies (all in flight at once); each warp takes a row at a
+//      time, each lane owns up to two hidden neurons (the paper's "each neuron
+//      on its own thread") with their incoming weights in registers, computes
+//      z1, h, the warp-shuffle sum z2, o (Eq. 1), the output delta and the
+//      hidden deltas, and accumulates the neuron's gradient row in registers;
+//      activations never leave the chip;
 //   2. warp partials are summed in shared memory in warp order and written as
 //      one partial per block;
-//   3. grid barrier; each thread then owns a slice of the parameters, sums the
-//      block partials in block order (deterministic), applies w -= lr g and
-//      adds g^2 to an FP64 norm partial;
-//   4. grid barrier; block 0 folds the FP64 loss and norm partials.
+//   3. grid barrier; every warp then owns a few parameters: its lanes load the
+//      block partials of a parameter in parallel (lane q takes blocks q, q+32,
+//      ...), add them in that order and finish with a butterfly -- a fixed
+//      order, so results are bitwise reproducible -- and lane 0 applies
+//      w -= lr g and adds g^2 to an FP64 norm partial;
+//   4. grid barrier; block 0 folds the FP64 loss and norm partials the same way.
+#include <mutex>
+
 #include "mlp_internal.cuh"
 
 namespace mlp {
@@ -23,7 +28,9 @@ namespace {
 constexpr int FNT = 256;         // threads per block
 constexpr int FNW = FNT / 32;    // warps per block
 constexpr int CAP = 64;          // rows staged in shared memory at a time
-constexpr int MAX_BLOCKS_PER_SM = 4;
+constexpr int QMAX = 5;          // blocks per lane in the cross-block sums
+constexpr int GMAX = 32 * QMAX;  // largest grid
+constexpr int PPW = 4;           // parameters per warp per round
 
 struct FArgs {
     int D, H;
@@ -47,17 +54,32 @@ struct FArgs {
 
 inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+// Shared-memory layout (floats): [weights staging | per-warp partials] (aliased),
+// then b1, w2, b2 staging, then CAP rows of X (DP wide, zero padded), CAP labels.
 __host__ __device__ inline int weights_floats(int D, int H) { return H * (D | 1); }
 __host__ __device__ inline int partial_floats(int D, int H) { return FNW * ((D + 2) * H + 1); }
-__host__ __device__ inline int xs_offset(int D, int H) {
+__host__ __device__ inline int bias_offset(int D, int H) {
     int a = weights_floats(D, H), b = partial_floats(D, H);
-    int m = a > b ? a : b;
-    return (m + 3) & ~3;
+    return ((a > b ? a : b) + 3) & ~3;
 }
+__host__ __device__ inline int xs_offset(int D, int H) { return (bias_offset(D, H) + 2 * H + 1 + 3) & ~3; }
 
 template <int DP>
 size_t smem_bytes(int D, int H) {
     return sizeof(float) * ((size_t)xs_offset(D, H) + (size_t)CAP * DP + CAP);
+}
+
+// Sum of v[q] for q < G in a fixed order: lane l adds q = l, l+32, ... in turn,
+// then a butterfly over the lanes.  Every lane returns the same value.
+template <typename T>
+__device__ __forceinline__ T fixed_sum(const T *__restrict__ v, int G, int lane) {
+    T s = T(0);
+#pragma unroll
+    for (int t = 0; t < QMAX; ++t) {
+        const int q = lane + 32 * t;
+        if (q < G) s += __ldcg(v + q);
+    }
+    return warp_sum(s);
 }
 
 template <int DP, int UPL, int ACT>
@@ -68,14 +90,19 @@ __global__ void __launch_bounds__(FNT, 1) k_fused_train(FArgs a) {
     const int HD = H * D;
     const int P = HD + 2 * H + 1;
     const int WSTR = D | 1;
-    float *Ws = smem;                       // weights staging, aliased with
-    float *parts = smem;                    // the per-warp partials
-    float *Xs = smem + xs_offset(D, H);     // CAP x DP rows (zero padded)
-    float *ys = Xs + CAP * DP;              // CAP labels
+    float *Ws = smem;                        // H x WSTR weights staging (aliased with
+    float *parts = smem;                     // the FNW x P per-warp partials)
+    float *Bs = smem + bias_offset(D, H);    // b1 [H], w2 [H], b2
+    float *Xs = smem + xs_offset(D, H);      // CAP x DP rows, zero padded
+    float *ys = Xs + CAP * DP;               // CAP labels
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int G = gridDim.x, g = blockIdx.x;
-    if (g == a.skip_block) return;          // fault-injection hook (tests only)
+    if (g == a.skip_block) return;           // fault-injection hook (tests only)
     unsigned nbar = 0;
+    const float *__restrict__ X = a.X;
+    const float *__restrict__ Y = a.y;
+    float *__restrict__ params = a.params;
+    float *__restrict__ part = a.part;
 
     for (int i = tid; i < CAP * DP; i += FNT) Xs[i] = 0.f;
 
@@ -87,13 +114,42 @@ __global__ void __launch_bounds__(FNT, 1) k_fused_train(FArgs a) {
         for (int64_t b0 = 0; b0 < a.n; b0 += mbs) {
             const int64_t m = min(mbs, a.n - b0);
             const float c = a.loss_mean ? 1.0f / (float)m : 1.0f;
+            const int64_t r0 = b0 + (m * g) / G, r1 = b0 + (m * (g + 1)) / G;
 
-            // ---- weights into shared memory, then into registers
+            // ---- stage the first rows asynchronously (X and y are read-only for
+            // the whole launch, so L1-allocating copies are safe) and the weights
+            // through L2 (other blocks rewrote them), eight loads in flight per
+            // thread
             __syncthreads();
-            for (int i = tid; i < HD; i += FNT) {
-                int j = i / D, k = i - j * D;
-                Ws[j * WSTR + k] = __ldcg(a.params + i);
+            int64_t cs = r0;
+            int cn = (int)min((int64_t)CAP, r1 - cs);
+            if (cn > 0) {
+                const float *Xg = X + cs * D;
+                for (int i = tid; i < cn * D; i += FNT) {
+                    const int s = i / D, k = i - s * D;
+                    cp_async4(Xs + s * DP + k, Xg + i);
+                }
+                for (int i = tid; i < cn; i += FNT) cp_async4(ys + i, Y + cs + i);
             }
+            for (int base = 0; base < P; base += 8 * FNT) {
+                float v[8];
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    const int i = base + r * FNT + tid;
+                    v[r] = (i < P) ? __ldcg(params + i) : 0.f;
+                }
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    const int i = base + r * FNT + tid;
+                    if (i < HD) {
+                        const int j = i / D, k = i - j * D;
+                        Ws[j * WSTR + k] = v[r];
+                    } else if (i < P) {
+                        Bs[i - HD] = v[r];
+                    }
+                }
+            }
+            cp_async_wait_all();
             __syncthreads();
             float w[UPL][DP], b1r[UPL], w2r[UPL];
 #pragma unroll
@@ -101,10 +157,10 @@ __global__ void __launch_bounds__(FNT, 1) k_fused_train(FArgs a) {
                 const int j = u * 32 + lane;
 #pragma unroll
                 for (int k = 0; k < DP; ++k) w[u][k] = (j < H && k < D) ? Ws[j * WSTR + k] : 0.f;
-                b1r[u] = (j < H) ? __ldcg(a.params + HD + j) : 0.f;
-                w2r[u] = (j < H) ? __ldcg(a.params + HD + H + j) : 0.f;
+                b1r[u] = (j < H) ? Bs[j] : 0.f;
+                w2r[u] = (j < H) ? Bs[H + j] : 0.f;
             }
-            const float b2 = __ldcg(a.params + P - 1);
+            const float b2 = Bs[2 * H];
 
             float acc[UPL][DP], gb1a[UPL], gw2a[UPL], gb2a = 0.f;
             double sse = 0.0;
@@ -117,17 +173,7 @@ __global__ void __launch_bounds__(FNT, 1) k_fused_train(FArgs a) {
             }
 
             // ---- forward + backward over this block's rows of the step
-            const int64_t r0 = b0 + (m * g) / G, r1 = b0 + (m * (g + 1)) / G;
-            for (int64_t cs = r0; cs < r1; cs += CAP) {
-                const int cn = (int)min((int64_t)CAP, r1 - cs);
-                __syncthreads();
-                const float *Xg = a.X + cs * D;
-                for (int i = tid; i < cn * D; i += FNT) {
-                    int s = i / D, k = i - s * D;
-                    Xs[s * DP + k] = Xg[i];
-                }
-                for (int i = tid; i < cn; i += FNT) ys[i] = a.y[cs + i];
-                __syncthreads();
+            while (cn > 0) {
                 for (int s = warp; s < cn; s += FNW) {
                     const float4 *xr = reinterpret_cast<const float4 *>(Xs + s * DP);
                     float z[UPL];
@@ -171,6 +217,19 @@ __global__ void __launch_bounds__(FNT, 1) k_fused_train(FArgs a) {
                         }
                     }
                 }
+                cs += cn;
+                cn = (int)min((int64_t)CAP, r1 - cs);
+                if (cn > 0) {
+                    __syncthreads();
+                    const float *Xg = X + cs * D;
+                    for (int i = tid; i < cn * D; i += FNT) {
+                        const int s = i / D, k = i - s * D;
+                        cp_async4(Xs + s * DP + k, Xg + i);
+                    }
+                    for (int i = tid; i < cn; i += FNT) cp_async4(ys + i, Y + cs + i);
+                    cp_async_wait_all();
+                    __syncthreads();
+                }
             }
 
             // ---- block partial: warp partials summed in warp order
@@ -192,7 +251,7 @@ __global__ void __launch_bounds__(FNT, 1) k_fused_train(FArgs a) {
                 s_red[warp] = sse;
             }
             __syncthreads();
-            float *pg = a.part + (int64_t)g * P;
+            float *pg = part + (int64_t)g * P;
             for (int p = tid; p < P; p += FNT) {
                 float s = parts[p];
 #pragma unroll
@@ -206,34 +265,43 @@ __global__ void __launch_bounds__(FNT, 1) k_fused_train(FArgs a) {
             }
             if (!grid_barrier(a.bar, (++nbar) * (unsigned)G, a.status)) return;
 
-            // ---- cross-block reduction in block order, update, norm partial
+            // ---- cross-block reduction in a fixed order, update, norm partial
             double gn = 0.0;
-            for (int64_t p = (int64_t)g * FNT + tid; p < P; p += (int64_t)G * FNT) {
-                float s = 0.f;
-                for (int q = 0; q < G; ++q) s += __ldcg(a.part + (int64_t)q * P + p);
-                a.params[p] = __ldcg(a.params + p) - a.lr * s;
-                gn += (double)s * (double)s;
+            const int64_t gw = (int64_t)g * FNW + warp;
+            for (int64_t p0 = gw * PPW; p0 < P; p0 += (int64_t)G * FNW * PPW) {
+                float v[PPW][QMAX];
+#pragma unroll
+                for (int i = 0; i < PPW; ++i)
+#pragma unroll
+                    for (int t = 0; t < QMAX; ++t) {
+                        const int q = lane + 32 * t;
+                        v[i][t] = (q < G && p0 + i < P) ? __ldcg(part + (int64_t)q * P + p0 + i) : 0.f;
+                    }
+                float old[PPW];
+#pragma unroll
+                for (int i = 0; i < PPW; ++i) old[i] = (lane == 0 && p0 + i < P) ? __ldcg(params + p0 + i) : 0.f;
+#pragma unroll
+                for (int i = 0; i < PPW; ++i) {
+                    float s = v[i][0];
+#pragma unroll
+                    for (int t = 1; t < QMAX; ++t) s += v[i][t];
+                    s = warp_sum(s);
+                    if (lane == 0 && p0 + i < P) {
+                        params[p0 + i] = old[i] - a.lr * s;
+                        gn += (double)s * (double)s;
+                    }
+                }
             }
-            gn = warp_sum(gn);
-            __syncthreads();
             if (lane == 0) s_red[warp] = gn;
             __syncthreads();
             if (tid == 0) {
                 double t = 0.0;
                 for (int q = 0; q < FNW; ++q) t += s_red[q];
                 a.gnp[g] = t;
-                if (g == 0) {
-                    double l = 0.0;
-                    for (int q = 0; q < G; ++q) l += __ldcg(a.lossp + q);
-                    sse_epoch += l;
-                }
             }
+            if (g == 0 && warp == 0) sse_epoch += fixed_sum(a.lossp, G, lane);
             if (!grid_barrier(a.bar, (++nbar) * (unsigned)G, a.status)) return;
-            if (g == 0 && tid == 0) {
-                double t = 0.0;
-                for (int q = 0; q < G; ++q) t += __ldcg(a.gnp + q);
-                gn_last = t;
-            }
+            if (g == 0 && warp == 0) gn_last = fixed_sum(a.gnp, G, lane);
         }
         if (g == 0 && tid == 0) {
             const double C = a.loss_mean ? (a.n > 0 ? 1.0 / (double)a.n : 0.0) : 1.0;
@@ -283,6 +351,38 @@ bool choose(int act, int D, int H, Choice *c) {
     return true;
 }
 
+// Resident blocks per SM for (kernel, dynamic smem) on the current device,
+// computed once (the attribute call and the occupancy query are not free).
+int blocks_per_sm(void *fn, size_t smem, cudaError_t *err) {
+    struct Entry {
+        void *fn;
+        size_t smem;
+        int dev;
+        int per_sm;
+    };
+    static std::mutex mu;
+    static Entry cache[64];
+    static int ncache = 0;
+    int dev = 0;
+    *err = cudaGetDevice(&dev);
+    if (*err != cudaSuccess) return 0;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        for (int i = 0; i < ncache; ++i)
+            if (cache[i].fn == fn && cache[i].smem == smem && cache[i].dev == dev) return cache[i].per_sm;
+    }
+    if (smem > 48 * 1024) {
+        *err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (*err != cudaSuccess) return 0;
+    }
+    int per_sm = 0;
+    *err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, FNT, smem);
+    if (*err != cudaSuccess) return 0;
+    std::lock_guard<std::mutex> lk(mu);
+    if (ncache < 64) cache[ncache++] = {fn, smem, dev, per_sm};
+    return per_sm;
+}
+
 }  // namespace
 
 bool fused_supported(int D, int H) {
@@ -297,17 +397,17 @@ size_t fused_scratch_bytes(int D, int H, int sms) {
 }
 
 void fused_scratch_carve(void *base, int D, int H, int sms, FusedScratch *s) {
+    (void)sms;
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    const size_t Gmax = (size_t)sms * MAX_BLOCKS_PER_SM;
     const size_t P = (size_t)(D + 2) * H + 1;
     char *b = (char *)base;
     size_t off = 0;
     s->part = (float *)(b + off);
-    off = al(off + sizeof(float) * Gmax * P);
+    off = al(off + sizeof(float) * GMAX * P);
     s->lossp = (double *)(b + off);
-    off = al(off + sizeof(double) * Gmax);
+    off = al(off + sizeof(double) * GMAX);
     s->gnp = (double *)(b + off);
-    off = al(off + sizeof(double) * Gmax);
+    off = al(off + sizeof(double) * GMAX);
     s->bar = (unsigned *)(b + off);
 }
 
@@ -318,20 +418,15 @@ cudaError_t fused_train(int act, int D, int H, int64_t n, const float *X, const 
     Choice ch;
     if (!choose(act, D, H, &ch)) return cudaErrorInvalidValue;
     cudaError_t e;
-    if (ch.smem > 48 * 1024) {
-        e = cudaFuncSetAttribute(ch.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ch.smem);
-        if (e != cudaSuccess) return e;
-    }
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ch.fn, FNT, ch.smem);
+    int per_sm = blocks_per_sm(ch.fn, ch.smem, &e);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    if (per_sm > MAX_BLOCKS_PER_SM) per_sm = MAX_BLOCKS_PER_SM;
     const int sms = device_sm_count();
     const int64_t mbs = (mb <= 0 || mb >= n) ? n : mb;
     if (rows_per_block < 1) rows_per_block = 64;
     int64_t G = cdiv(mbs > 0 ? mbs : 1, rows_per_block);
     if (G > (int64_t)per_sm * sms) G = (int64_t)per_sm * sms;
+    if (G > GMAX) G = GMAX;
     if (G < 1) G = 1;
     if (grid_used) *grid_used = (int)G;
     const int64_t steps_per_epoch = n > 0 ? cdiv(n, mbs) : 0;

@@ -70,6 +70,16 @@ __device__ __forceinline__ int ld_volatile(const int *p) {
     return *(const volatile int *)p;
 }
 
+// 4-byte asynchronous global -> shared copy (all copies of a thread stay in
+// flight until cp_async_wait_all).
+__device__ __forceinline__ void cp_async4(void *smem_dst, const void *gmem_src) {
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
 template <typename T> __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
@@ -177,6 +187,25 @@ cudaError_t fused_train(int act, int D, int H, int64_t n, const float *X, const 
                         double *loss_hist, double *gnorm_hist, int *status,
                         const FusedScratch &s, int rows_per_block, int skip_block,
                         cudaStream_t st, int *grid_used);
+
+// ------------------------------------------------------ batched-path launcher
+
+// One network of a batch, as the kernel reads it (device memory).
+struct BatchNet {
+    const float *X;      // n x D rows
+    const float *y;      // n labels
+    float *params;       // packed [W1, b1, w2, b2], trained in place
+    double *loss_hist;   // [epochs] or NULL
+    int64_t n;
+    int32_t H;
+    int32_t pad;
+};
+
+int batched_max_H();
+int batched_max_D();
+void batched_smem_layout(int D, int Hmax, int *part_floats, int *wm_floats, size_t *bytes);
+cudaError_t batched_train(int act, int D, int Hmax, const BatchNet *nets_dev, const int *order_dev, int n_nets,
+                          int epochs, float lr, int loss_mean, int *status, cudaStream_t st);
 
 int device_sm_count();
 

@@ -177,7 +177,7 @@ def test_fp64_path_matches_oracle_tightly():
         net.set([a.astype(np.float64) for a in W])
         lh = t.zeros(10, dtype=t.float64, device="cuda")
         B.mlp_train_epochs(net.h, dev(X), dev(y.astype(np.float64)), n, 10, 0, lh, None, stream())
-        q, lh_ref, _ = oracle.train(X, y, Params(*W), 0.1, 10)
+        q, lh_ref, _ = oracle.train(X, y, Params(*W), lr32(), 10)  # the handle stores lr as float
         assert rel_err_norm(net.flat(), q.flat()) <= 1e-12
         assert rel_err_elem(host(lh), lh_ref) <= 1e-12
 
