@@ -181,10 +181,13 @@ mlp_status mlp_set_rows_per_block(mlp_t net, int32_t rows);
 /*
  * Many independent networks trained in one launch (the paper trains its male
  * and female subsets as separate networks, Sec. 2.1; here any number, each with
- * its own H and n).  Every field is read on the host; X, y, params and
- * loss_hist point to device memory.  params holds the net's packed weights
- * [W1 (H x D), b1, w2, b2] (float), trained in place; loss_hist [epochs] may be
- * NULL.  All nets share D, epochs, lr, loss_mean and full-batch updates.
+ * its own H and n).  All nets share D, the activation, lr, the loss scaling and
+ * full-batch gradient descent (Sec. 2.2).  Each descriptor names device memory:
+ * X (n x D row-major, float), y (n floats), params (the net's packed weights
+ * [W1 (H x D), b1, w2, b2], float, trained in place) and loss_hist (epochs
+ * doubles, may be NULL; receives the loss before each epoch's update).
+ * Limits of this build: MLP_FP32, D <= 64, H <= 128; n is unbounded (rows
+ * beyond 256 are streamed from device memory each epoch).
  */
 typedef struct {
     int32_t H;
@@ -195,6 +198,29 @@ typedef struct {
     double *loss_hist;
 } mlp_net_desc;
 
+typedef struct mlp_batch *mlp_batch_t;
+
+/* Validate the descriptors (read on the host), copy them to device memory
+ * owned by the plan, ordered by cost, largest first.  The buffers they name
+ * must stay valid while the plan is run. */
+mlp_status mlp_batch_create(int32_t prec, int32_t act, int32_t D,
+                            const mlp_net_desc *nets, int32_t n_nets, float lr,
+                            int32_t loss_mean, mlp_batch_t *out);
+
+/* Train every net of the plan for `epochs` epochs: one kernel launch, no
+ * allocation and no host synchronisation, so it can be captured in a CUDA
+ * graph.  Each loss_hist must hold `epochs` doubles. */
+mlp_status mlp_batch_run(mlp_batch_t b, int32_t epochs, void *stream);
+
+/* Synchronise `stream`, then return and clear the plan's device status
+ * (MLP_OK or MLP_ENONFINITE). */
+mlp_status mlp_batch_check(mlp_batch_t b, void *stream);
+
+/* Free the plan (not the buffers its descriptors name).  NULL is ignored. */
+void mlp_batch_destroy(mlp_batch_t b);
+
+/* mlp_batch_create + mlp_batch_run + mlp_batch_check + mlp_batch_destroy.
+ * Synchronous. */
 mlp_status mlp_batch_train(int32_t prec, int32_t act, int32_t D,
                            const mlp_net_desc *nets, int32_t n_nets,
                            int32_t epochs, float lr, int32_t loss_mean,

@@ -25,6 +25,7 @@ EXPORTS = [
     "mlp_forward", "mlp_backward", "mlp_update", "mlp_step_plain", "mlp_train_epochs",
     "mlp_train_host", "mlp_predict", "mlp_check", "mlp_workspace_bytes", "mlp_forward_w",
     "mlp_backward_w", "mlp_debug_skip_block", "mlp_set_rows_per_block", "mlp_batch_train",
+    "mlp_batch_create", "mlp_batch_run", "mlp_batch_check", "mlp_batch_destroy",
     "mlp_last_error", "mlp_version",
 ]
 
@@ -84,6 +85,10 @@ def lib():
             "mlp_debug_skip_block": (S, [V, I32]),
             "mlp_set_rows_per_block": (S, [V, I32]),
             "mlp_batch_train": (S, [I32, I32, I32, ctypes.POINTER(mlp_net_desc), I32, I32, F, I32, V]),
+            "mlp_batch_create": (S, [I32, I32, I32, ctypes.POINTER(mlp_net_desc), I32, F, I32, ctypes.POINTER(V)]),
+            "mlp_batch_run": (S, [V, I32, V]),
+            "mlp_batch_check": (S, [V, V]),
+            "mlp_batch_destroy": (None, [V]),
             "mlp_last_error": (ctypes.c_char_p, []),
             "mlp_version": (ctypes.c_char_p, []),
         }
@@ -202,8 +207,28 @@ def mlp_backward_w(prec, act, D, H, n, X, W1, w2, hid, o, dLdo, gW1, gb1, gw2, g
 
 
 def mlp_batch_train(prec, act, D, descs, epochs, lr, loss_mean=1, stream=0):
-    arr = (mlp_net_desc * len(descs))(*descs)
+    arr = (mlp_net_desc * max(len(descs), 1))(*descs)
     return _ck(lib().mlp_batch_train(prec, act, D, arr, len(descs), epochs, lr, loss_mean, stream))
+
+
+def mlp_batch_create(prec, act, D, descs, lr, loss_mean=1):
+    arr = (mlp_net_desc * max(len(descs), 1))(*descs)
+    b = ctypes.c_void_p()
+    _ck(lib().mlp_batch_create(prec, act, D, arr, len(descs), lr, loss_mean, ctypes.byref(b)))
+    return b.value
+
+
+def mlp_batch_run(b, epochs, stream=0):
+    return _ck(lib().mlp_batch_run(b, epochs, stream))
+
+
+def mlp_batch_check(b, stream=0):
+    """Returns the status code (does not raise)."""
+    return lib().mlp_batch_check(b, stream)
+
+
+def mlp_batch_destroy(b):
+    lib().mlp_batch_destroy(b)
 
 
 def mlp_last_error():

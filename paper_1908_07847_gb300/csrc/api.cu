@@ -6,6 +6,8 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <algorithm>
+#include <vector>
 
 #include "mlp_internal.cuh"
 
@@ -460,18 +462,122 @@ mlp_status mlp_backward_w(int32_t prec, int32_t act, int32_t D, int32_t H, int64
     return MLP_OK;
 }
 
+}  // extern "C"
+
+struct mlp_batch {
+    int device;
+    int act, D, Hmax, n_nets;
+    float lr;
+    int loss_mean;
+    void *mem;                 // one allocation: nets, order, status
+    mlp::BatchNet *nets;
+    int *order;
+    int *status;
+};
+
+extern "C" {
+
+mlp_status mlp_batch_create(int32_t prec, int32_t act, int32_t D, const mlp_net_desc *nets, int32_t n_nets,
+                            float lr, int32_t loss_mean, mlp_batch_t *out) {
+    if (!out) return fail(MLP_EINVAL, "mlp_batch_create: null out");
+    *out = nullptr;
+    if (prec != MLP_FP32) return fail(MLP_EUNSUPPORTED, "mlp_batch_create: only MLP_FP32 in this build");
+    if (act != MLP_ACT_SIGMOID && act != MLP_ACT_TANH) return fail(MLP_EINVAL, "mlp_batch_create: bad act");
+    if (D < 1 || D > mlp::batched_max_D()) return fail(MLP_EINVAL, "mlp_batch_create: D=%d out of 1..64", D);
+    if (n_nets < 0 || (n_nets > 0 && !nets)) return fail(MLP_EINVAL, "mlp_batch_create: bad net list");
+    int Hmax = 1;
+    std::vector<mlp::BatchNet> host(n_nets);
+    std::vector<double> cost(n_nets);
+    for (int t = 0; t < n_nets; ++t) {
+        const mlp_net_desc &d = nets[t];
+        if (d.H < 1 || d.H > mlp::batched_max_H())
+            return fail(MLP_EINVAL, "mlp_batch_create: net %d has H=%d out of 1..128", t, d.H);
+        if (d.n < 0 || !d.params || (d.n > 0 && (!d.X || !d.y)))
+            return fail(MLP_EINVAL, "mlp_batch_create: net %d has a null buffer or n < 0", t);
+        Hmax = d.H > Hmax ? d.H : Hmax;
+        host[t] = {(const float *)d.X, d.y, d.params, d.loss_hist, d.n, d.H, 0};
+        // lanes busy per row: a power-of-two segment up to 32, else 32 per 32 units
+        int lanes = d.H <= 32 ? 4 : 32 * ((d.H + 31) / 32);
+        while (d.H <= 32 && lanes < d.H) lanes <<= 1;
+        cost[t] = (double)d.n * lanes;
+    }
+    std::vector<int> order(n_nets);
+    for (int t = 0; t < n_nets; ++t) order[t] = t;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    mlp_batch_t b = new (std::nothrow) mlp_batch();
+    if (!b) return fail(MLP_ENOMEM, "mlp_batch_create: host allocation");
+    if (cudaGetDevice(&b->device) != cudaSuccess) {
+        delete b;
+        return fail(MLP_ECUDA, "mlp_batch_create: no device");
+    }
+    b->act = act;
+    b->D = D;
+    b->Hmax = Hmax;
+    b->n_nets = n_nets;
+    b->lr = lr;
+    b->loss_mean = loss_mean ? 1 : 0;
+    const size_t nb = ((sizeof(mlp::BatchNet) * (size_t)(n_nets > 0 ? n_nets : 1)) + 255) & ~(size_t)255;
+    const size_t ob = ((sizeof(int) * (size_t)(n_nets > 0 ? n_nets : 1)) + 255) & ~(size_t)255;
+    if (cudaMalloc(&b->mem, nb + ob + 256) != cudaSuccess) {
+        cudaGetLastError();
+        delete b;
+        return fail(MLP_ENOMEM, "mlp_batch_create: device allocation");
+    }
+    b->nets = (mlp::BatchNet *)b->mem;
+    b->order = (int *)((char *)b->mem + nb);
+    b->status = (int *)((char *)b->mem + nb + ob);
+    cudaError_t e = cudaSuccess;
+    if (n_nets > 0) {
+        e = cudaMemcpy(b->nets, host.data(), sizeof(mlp::BatchNet) * n_nets, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(b->order, order.data(), sizeof(int) * n_nets, cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) e = cudaMemset(b->status, 0, sizeof(int));
+    if (e != cudaSuccess) {
+        cudaFree(b->mem);
+        delete b;
+        return cuda_fail(e, "mlp_batch_create");
+    }
+    *out = b;
+    return MLP_OK;
+}
+
+mlp_status mlp_batch_run(mlp_batch_t b, int32_t epochs, void *stream) {
+    if (!b) return fail(MLP_EINVAL, "mlp_batch_run: null plan");
+    if (epochs < 0) return fail(MLP_EINVAL, "mlp_batch_run: epochs < 0");
+    DeviceScope ds(b->device);
+    CK(mlp::batched_train(b->act, b->D, b->Hmax, b->nets, b->order, b->n_nets, epochs, b->lr, b->loss_mean,
+                          b->status, (cudaStream_t)stream),
+       "batched training kernel");
+    return MLP_OK;
+}
+
+mlp_status mlp_batch_check(mlp_batch_t b, void *stream) {
+    if (!b) return fail(MLP_EINVAL, "mlp_batch_check: null plan");
+    DeviceScope ds(b->device);
+    CK(cudaStreamSynchronize((cudaStream_t)stream), "mlp_batch_check sync");
+    int st = 0;
+    CK(cudaMemcpy(&st, b->status, sizeof(int), cudaMemcpyDeviceToHost), "mlp_batch_check read");
+    CK(cudaMemset(b->status, 0, sizeof(int)), "mlp_batch_check clear");
+    if (st & mlp::ST_NONFINITE) return fail(MLP_ENONFINITE, "a net's loss was not finite");
+    return MLP_OK;
+}
+
+void mlp_batch_destroy(mlp_batch_t b) {
+    if (!b) return;
+    DeviceScope ds(b->device);
+    cudaFree(b->mem);
+    delete b;
+}
+
 mlp_status mlp_batch_train(int32_t prec, int32_t act, int32_t D, const mlp_net_desc *nets, int32_t n_nets,
                            int32_t epochs, float lr, int32_t loss_mean, void *stream) {
-    (void)prec;
-    (void)act;
-    (void)D;
-    (void)nets;
-    (void)n_nets;
-    (void)epochs;
-    (void)lr;
-    (void)loss_mean;
-    (void)stream;
-    return fail(MLP_EUNSUPPORTED, "mlp_batch_train: not built yet");
+    mlp_batch_t b = nullptr;
+    mlp_status s = mlp_batch_create(prec, act, D, nets, n_nets, lr, loss_mean, &b);
+    if (s) return s;
+    s = mlp_batch_run(b, epochs, stream);
+    if (s == MLP_OK) s = mlp_batch_check(b, stream);
+    mlp_batch_destroy(b);
+    return s;
 }
 
 }  // extern "C"

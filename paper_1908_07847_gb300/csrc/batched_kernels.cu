@@ -2,47 +2,30 @@
 // the male and female subsets as separate networks; here thousands of nets with
 // their own hidden width H <= 128 and row count n).  One block trains one net
 // for all epochs without leaving the chip: its rows of X (when they fit) and
-// its master weights live in shared memory, each lane owns one or two hidden
-// neurons with their incoming weights and gradient rows in registers, and the
-// per-epoch gradient reduction and update (Sec. 2.2: full-batch gradient
-// descent, no momentum) run in shared memory in a fixed order.
-//
-// Small widths pack several rows into one warp: a warp is cut into segments of
-// S = next power of two >= H lanes (S >= 4), lane j of a segment owns hidden
-// unit j, and the output sum z2 is a butterfly over the segment.  Widths 65..128
-// use two warps per row group that exchange their halves of z2 through shared
-// memory.  Blocks take nets in the order given (the host sorts by cost,
-// longest first).
-#include "mlp_internal.cuh"
+// its master weights live in shared memory, the row engine (row_engine.cuh)
+// runs forward and backward with one hidden neuron per lane, and the per-epoch
+// gradient reduction and update (Sec. 2.2: full-batch gradient descent, no
+// momentum) run in shared memory in a fixed order.  Blocks take nets in the
+// order given (the host sorts them by cost, largest first).
+#include "row_engine.cuh"
 
 namespace mlp {
 
 namespace {
 
-constexpr int BNW = 4;           // warps per block
-constexpr int BNT = BNW * 32;    // threads per block
-constexpr int RB = 4;            // rows per lane slot per iteration
+constexpr int BNT = RE_NT;       // threads per block
 constexpr int BCAP = 256;        // rows staged in shared memory at a time
 
-inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
-
-template <int DP, int UPL, int WU, int ACT>
+template <int DP, int WU, int ACT>
 __device__ __forceinline__ void net_body(const BatchNet &nd, int D, int epochs, float lr, int loss_mean,
                                          int *status, float *Xs, float *ys, float *Wm, float *part,
                                          float *zx, double *s_sse) {
-    const int H = nd.H;
+    RowEngine<DP, WU, ACT> eng;
+    eng.setup(nd.H, D);
+    constexpr int NG = RowEngine<DP, WU, ACT>::NG;
     const int64_t n = nd.n;
-    const int HD = H * D, P = HD + 2 * H + 1;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    constexpr int NG = BNW / WU;  // row groups per block
-    const int grp = warp / WU, wu = warp % WU;
-    int S = 32;
-    if (UPL == 1 && WU == 1) {
-        S = 4;
-        while (S < H) S <<= 1;
-    }
-    const int slot = lane / S, sl = lane % S, nslots = 32 / S;
-    const int RPI = nslots * RB;  // rows per group iteration
+    const int P = (D + 2) * nd.H + 1;
+    const int tid = threadIdx.x;
 
     for (int i = tid; i < P; i += BNT) Wm[i] = nd.params[i];
     const bool resident = n <= BCAP;
@@ -58,32 +41,9 @@ __device__ __forceinline__ void net_body(const BatchNet &nd, int D, int epochs, 
     __syncthreads();
     const float c = loss_mean ? 1.0f / (float)n : 1.0f;
     const double C = loss_mean ? 1.0 / (double)n : 1.0;
-    int par = 0;
 
     for (int e = 0; e < epochs; ++e) {
-        float w[UPL][DP], b1r[UPL], w2r[UPL];
-        int jj[UPL];
-#pragma unroll
-        for (int u = 0; u < UPL; ++u) {
-            const int j = wu * (32 * UPL) + u * 32 + sl;
-            jj[u] = j;
-            const bool ok = j < H;
-#pragma unroll
-            for (int k = 0; k < DP; ++k) w[u][k] = (ok && k < D) ? Wm[j * D + k] : 0.f;
-            b1r[u] = ok ? Wm[HD + j] : 0.f;
-            w2r[u] = ok ? Wm[HD + H + j] : 0.f;
-        }
-        const float b2 = Wm[P - 1];
-        float acc[UPL][DP], gb1a[UPL], gw2a[UPL], gb2a = 0.f;
-        double sse = 0.0;
-#pragma unroll
-        for (int u = 0; u < UPL; ++u) {
-            gb1a[u] = 0.f;
-            gw2a[u] = 0.f;
-#pragma unroll
-            for (int k = 0; k < DP; ++k) acc[u][k] = 0.f;
-        }
-
+        eng.load_weights(Wm);
         for (int64_t cs = 0; cs < n; cs += BCAP) {
             const int cn = (int)min((int64_t)BCAP, n - cs);
             if (!resident) {
@@ -91,119 +51,9 @@ __device__ __forceinline__ void net_body(const BatchNet &nd, int D, int epochs, 
                 load_rows(cs, cn);
                 __syncthreads();
             }
-            for (int base = grp * RPI; base < cn; base += NG * RPI) {
-                int r[RB];
-                bool valid[RB];
-#pragma unroll
-                for (int t = 0; t < RB; ++t) {
-                    const int rr = base + slot * RB + t;
-                    valid[t] = rr < cn;
-                    r[t] = valid[t] ? rr : 0;
-                }
-                float z[RB][UPL];
-#pragma unroll
-                for (int t = 0; t < RB; ++t)
-#pragma unroll
-                    for (int u = 0; u < UPL; ++u) z[t][u] = b1r[u];
-#pragma unroll
-                for (int q = 0; q < DP / 4; ++q) {
-#pragma unroll
-                    for (int t = 0; t < RB; ++t) {
-                        const float4 xv = *reinterpret_cast<const float4 *>(Xs + r[t] * DP + 4 * q);
-#pragma unroll
-                        for (int u = 0; u < UPL; ++u) {
-                            z[t][u] = fmaf(xv.x, w[u][4 * q + 0], z[t][u]);
-                            z[t][u] = fmaf(xv.y, w[u][4 * q + 1], z[t][u]);
-                            z[t][u] = fmaf(xv.z, w[u][4 * q + 2], z[t][u]);
-                            z[t][u] = fmaf(xv.w, w[u][4 * q + 3], z[t][u]);
-                        }
-                    }
-                }
-                float hv[RB][UPL], zp[RB];
-#pragma unroll
-                for (int t = 0; t < RB; ++t) {
-                    zp[t] = 0.f;
-#pragma unroll
-                    for (int u = 0; u < UPL; ++u) {
-                        hv[t][u] = Act<ACT>::f(z[t][u]);
-                        zp[t] = fmaf(hv[t][u], w2r[u], zp[t]);
-                    }
-                }
-#pragma unroll
-                for (int t = 0; t < RB; ++t)
-                    for (int off = S >> 1; off > 0; off >>= 1) zp[t] += __shfl_xor_sync(0xffffffffu, zp[t], off);
-                if (WU == 2) {
-                    float *zg = zx + (par * NG + grp) * (2 * RB);
-                    if (lane == 0) {
-#pragma unroll
-                        for (int t = 0; t < RB; ++t) zg[wu * RB + t] = zp[t];
-                    }
-                    asm volatile("bar.sync %0, %1;" ::"r"(1 + grp), "r"(64) : "memory");
-#pragma unroll
-                    for (int t = 0; t < RB; ++t) zp[t] = zg[t] + zg[RB + t];
-                    par ^= 1;
-                }
-#pragma unroll
-                for (int t = 0; t < RB; ++t) {
-                    const float o = sigmoid_out(zp[t] + b2);
-                    const float err = o - ys[r[t]];
-                    const float d2 = valid[t] ? c * err * o * (1.0f - o) : 0.f;
-                    if (valid[t]) sse += (double)err * (double)err;
-                    gb2a += d2;
-#pragma unroll
-                    for (int u = 0; u < UPL; ++u) {
-                        gw2a[u] = fmaf(d2, hv[t][u], gw2a[u]);
-                        const float d1 = d2 * w2r[u] * Act<ACT>::df(hv[t][u]);
-                        gb1a[u] += d1;
-                        hv[t][u] = d1;
-                    }
-                }
-#pragma unroll
-                for (int q = 0; q < DP / 4; ++q) {
-#pragma unroll
-                    for (int t = 0; t < RB; ++t) {
-                        const float4 xv = *reinterpret_cast<const float4 *>(Xs + r[t] * DP + 4 * q);
-#pragma unroll
-                        for (int u = 0; u < UPL; ++u) {
-                            acc[u][4 * q + 0] = fmaf(hv[t][u], xv.x, acc[u][4 * q + 0]);
-                            acc[u][4 * q + 1] = fmaf(hv[t][u], xv.y, acc[u][4 * q + 1]);
-                            acc[u][4 * q + 2] = fmaf(hv[t][u], xv.z, acc[u][4 * q + 2]);
-                            acc[u][4 * q + 3] = fmaf(hv[t][u], xv.w, acc[u][4 * q + 3]);
-                        }
-                    }
-                }
-            }
+            eng.rows(Xs, ys, cn, c, zx);
         }
-        // Sum the row slots of each warp (segments), fixed butterfly order.
-        for (int off = S; off < 32; off <<= 1) {
-#pragma unroll
-            for (int u = 0; u < UPL; ++u) {
-#pragma unroll
-                for (int k = 0; k < DP; ++k) acc[u][k] += __shfl_xor_sync(0xffffffffu, acc[u][k], off);
-                gb1a[u] += __shfl_xor_sync(0xffffffffu, gb1a[u], off);
-                gw2a[u] += __shfl_xor_sync(0xffffffffu, gw2a[u], off);
-            }
-            gb2a += __shfl_xor_sync(0xffffffffu, gb2a, off);
-            sse += __shfl_xor_sync(0xffffffffu, sse, off);
-        }
-        float *pg = part + grp * P;
-        if (slot == 0) {
-#pragma unroll
-            for (int u = 0; u < UPL; ++u) {
-                const int j = jj[u];
-                if (j < H) {
-#pragma unroll
-                    for (int k = 0; k < DP; ++k)
-                        if (k < D) pg[j * D + k] = acc[u][k];
-                    pg[HD + j] = gb1a[u];
-                    pg[HD + H + j] = gw2a[u];
-                }
-            }
-        }
-        if (wu == 0 && lane == 0) {
-            pg[P - 1] = gb2a;
-            s_sse[grp] = sse;
-        }
+        eng.write_group(part, s_sse);
         __syncthreads();
         for (int p = tid; p < P; p += BNT) {
             float g = part[p];
@@ -225,17 +75,17 @@ __device__ __forceinline__ void net_body(const BatchNet &nd, int D, int epochs, 
 }
 
 template <int DP, int ACT>
-__global__ void __launch_bounds__(BNT, 2) k_batched_train(const BatchNet *__restrict__ nets,
+__global__ void __launch_bounds__(BNT, (DP <= 36 ? 2 : 1)) k_batched_train(const BatchNet *__restrict__ nets,
                                                          const int *__restrict__ order, int n_nets, int D,
                                                          int epochs, float lr, int loss_mean, int *status,
                                                          int part_floats, int wm_floats) {
     extern __shared__ __align__(16) float smem[];
-    __shared__ double s_sse[BNW];
+    __shared__ double s_sse[RE_NW];
     float *Xs = smem;                      // BCAP x DP
     float *ys = Xs + BCAP * DP;            // BCAP
     float *Wm = ys + BCAP;                 // wm_floats
     float *part = Wm + wm_floats;          // part_floats
-    float *zx = part + part_floats;        // 2 x 2 x 2 x RB
+    float *zx = part + part_floats;        // z2 exchange
     for (int i = threadIdx.x; i < BCAP * DP; i += BNT) Xs[i] = 0.f;
     __syncthreads();
     for (int idx = blockIdx.x; idx < n_nets; idx += gridDim.x) {
@@ -246,11 +96,11 @@ __global__ void __launch_bounds__(BNT, 2) k_batched_train(const BatchNet *__rest
             continue;
         }
         if (nd.H <= 32)
-            net_body<DP, 1, 1, ACT>(nd, D, epochs, lr, loss_mean, status, Xs, ys, Wm, part, zx, s_sse);
+            net_body<DP, 1, ACT>(nd, D, epochs, lr, loss_mean, status, Xs, ys, Wm, part, zx, s_sse);
         else if (nd.H <= 64)
-            net_body<DP, 2, 1, ACT>(nd, D, epochs, lr, loss_mean, status, Xs, ys, Wm, part, zx, s_sse);
+            net_body<DP, 2, ACT>(nd, D, epochs, lr, loss_mean, status, Xs, ys, Wm, part, zx, s_sse);
         else
-            net_body<DP, 2, 2, ACT>(nd, D, epochs, lr, loss_mean, status, Xs, ys, Wm, part, zx, s_sse);
+            net_body<DP, 4, ACT>(nd, D, epochs, lr, loss_mean, status, Xs, ys, Wm, part, zx, s_sse);
     }
 }
 
@@ -276,19 +126,11 @@ int batched_max_D() { return 64; }
 
 void batched_smem_layout(int D, int Hmax, int *part_floats, int *wm_floats, size_t *bytes) {
     const int DP = dp_for(D);
-    // Row groups: 4 for H <= 64, 2 for 65..128 (two warps per group).
-    int pf = 0;
-    for (int H : {32, 64, Hmax}) {
-        if (H > Hmax) continue;
-        const int P = (D + 2) * H + 1;
-        const int NG = (H <= 64) ? BNW : BNW / 2;
-        pf = pf > NG * P ? pf : NG * P;
-    }
+    const int pf = re_part_floats(D, Hmax);
     const int wm = ((D + 2) * Hmax + 1 + 3) & ~3;
-    pf = (pf + 3) & ~3;
     *part_floats = pf;
     *wm_floats = wm;
-    *bytes = sizeof(float) * ((size_t)BCAP * DP + BCAP + wm + pf + 2 * 2 * 2 * RB);
+    *bytes = sizeof(float) * ((size_t)BCAP * DP + BCAP + wm + pf + RE_ZX);
 }
 
 cudaError_t batched_train(int act, int D, int Hmax, const BatchNet *nets_dev, const int *order_dev, int n_nets,

@@ -1,32 +1,31 @@
-// Fused training kernel for small networks (D <= 64, H <= 64): one cooperative
+// Fused training kernel for small networks (D <= 64, H <= 128): one cooperative
 // launch runs every step of every epoch.  Per step (Sec. 2.2 of arXiv
 // 1908.07847: feed-forward, output error, backpropagation, gradient descent
 // with no momentum):
-//   1. every block stages the weights and its rows of X in shared memory with
-//      asynchronous copies (all in flight at once); each warp takes a row at a
-//      time, each lane owns up to two hidden neurons (the paper's "each neuron
-//      on its own thread") with their incoming weights in registers, computes
-//      z1, h, the warp-shuffle sum z2, o (Eq. 1), the output delta and the
-//      hidden deltas, and accumulates the neuron's gradient row in registers;
-//      activations never leave the chip;
-//   2. warp partials are summed in shared memory in warp order and written as
-//      one partial per block;
+//   1. every block stages the packed weights (through L2: other blocks rewrote
+//      them) and its rows of X (asynchronous copies) in shared memory; the row
+//      engine (row_engine.cuh) runs forward and backward with one hidden neuron
+//      per lane and accumulates the gradient rows in registers; activations
+//      never leave the chip;
+//   2. row-group partials are summed in shared memory in group order and
+//      written as one partial per block;
 //   3. grid barrier; every warp then owns a few parameters: its lanes load the
 //      block partials of a parameter in parallel (lane q takes blocks q, q+32,
 //      ...), add them in that order and finish with a butterfly -- a fixed
 //      order, so results are bitwise reproducible -- and lane 0 applies
 //      w -= lr g and adds g^2 to an FP64 norm partial;
-//   4. grid barrier; block 0 folds the FP64 loss and norm partials the same way.
+//   4. grid barrier before the next step; after the launch's last step the
+//      last block to finish (arrival ticket) folds the FP64 loss and norm
+//      partials instead, so a one-step launch waits on one barrier only.
 #include <mutex>
 
-#include "mlp_internal.cuh"
+#include "row_engine.cuh"
 
 namespace mlp {
 
 namespace {
 
-constexpr int FNT = 256;         // threads per block
-constexpr int FNW = FNT / 32;    // warps per block
+constexpr int FNT = RE_NT;       // threads per block
 constexpr int CAP = 64;          // rows staged in shared memory at a time
 constexpr int QMAX = 5;          // blocks per lane in the cross-block sums
 constexpr int GMAX = 32 * QMAX;  // largest grid
@@ -48,25 +47,20 @@ struct FArgs {
     float *part;
     double *lossp;
     double *gnp;
-    unsigned *bar;
+    double *epoch_sse;
+    unsigned *bar;   // [0]: barrier arrivals, [1]: last-step finish tickets
     int skip_block;
 };
 
 inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
-// Shared-memory layout (floats): [weights staging | per-warp partials] (aliased),
-// then b1, w2, b2 staging, then CAP rows of X (DP wide, zero padded), CAP labels.
-__host__ __device__ inline int weights_floats(int D, int H) { return H * (D | 1); }
-__host__ __device__ inline int partial_floats(int D, int H) { return FNW * ((D + 2) * H + 1); }
-__host__ __device__ inline int bias_offset(int D, int H) {
-    int a = weights_floats(D, H), b = partial_floats(D, H);
-    return ((a > b ? a : b) + 3) & ~3;
-}
-__host__ __device__ inline int xs_offset(int D, int H) { return (bias_offset(D, H) + 2 * H + 1 + 3) & ~3; }
+// Shared-memory layout (floats): packed weights [P], row-group partials
+// [NG x P], CAP rows of X (DP wide, zero padded), CAP labels, z2 exchange.
+__host__ __device__ inline int wm_floats(int D, int H) { return ((D + 2) * H + 1 + 3) & ~3; }
 
 template <int DP>
 size_t smem_bytes(int D, int H) {
-    return sizeof(float) * ((size_t)xs_offset(D, H) + (size_t)CAP * DP + CAP);
+    return sizeof(float) * ((size_t)wm_floats(D, H) + re_part_floats(D, H) + (size_t)CAP * DP + CAP + RE_ZX);
 }
 
 // Sum of v[q] for q < G in a fixed order: lane l adds q = l, l+32, ... in turn,
@@ -82,27 +76,30 @@ __device__ __forceinline__ T fixed_sum(const T *__restrict__ v, int G, int lane)
     return warp_sum(s);
 }
 
-template <int DP, int UPL, int ACT>
+template <int DP, int WU, int ACT>
 __global__ void __launch_bounds__(FNT, 1) k_fused_train(FArgs a) {
     extern __shared__ __align__(16) float smem[];
-    __shared__ double s_red[FNW];
+    __shared__ double s_red[RE_NW];
+    __shared__ int s_last;
+    using Eng = RowEngine<DP, WU, ACT>;
+    constexpr int NG = Eng::NG;
     const int D = a.D, H = a.H;
-    const int HD = H * D;
-    const int P = HD + 2 * H + 1;
-    const int WSTR = D | 1;
-    float *Ws = smem;                        // H x WSTR weights staging (aliased with
-    float *parts = smem;                     // the FNW x P per-warp partials)
-    float *Bs = smem + bias_offset(D, H);    // b1 [H], w2 [H], b2
-    float *Xs = smem + xs_offset(D, H);      // CAP x DP rows, zero padded
-    float *ys = Xs + CAP * DP;               // CAP labels
+    const int P = (D + 2) * H + 1;
+    float *Wm = smem;                               // packed weights
+    float *gpart = Wm + wm_floats(D, H);            // NG x P row-group partials
+    float *Xs = gpart + re_part_floats(D, H);       // CAP x DP rows
+    float *ys = Xs + CAP * DP;                      // CAP labels
+    float *zx = ys + CAP;                           // z2 exchange
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int G = gridDim.x, g = blockIdx.x;
-    if (g == a.skip_block) return;           // fault-injection hook (tests only)
+    if (g == a.skip_block) return;                  // fault-injection hook (tests only)
     unsigned nbar = 0;
     const float *__restrict__ X = a.X;
     const float *__restrict__ Y = a.y;
     float *__restrict__ params = a.params;
     float *__restrict__ part = a.part;
+    Eng eng;
+    eng.setup(H, D);
 
     for (int i = tid; i < CAP * DP; i += FNT) Xs[i] = 0.f;
 
@@ -113,13 +110,14 @@ __global__ void __launch_bounds__(FNT, 1) k_fused_train(FArgs a) {
         sse_epoch = 0.0;
         for (int64_t b0 = 0; b0 < a.n; b0 += mbs) {
             const int64_t m = min(mbs, a.n - b0);
+            const bool last_step = (e == a.epochs - 1) && (b0 + mbs >= a.n);
             const float c = a.loss_mean ? 1.0f / (float)m : 1.0f;
             const int64_t r0 = b0 + (m * g) / G, r1 = b0 + (m * (g + 1)) / G;
 
             // ---- stage the first rows asynchronously (X and y are read-only for
-            // the whole launch, so L1-allocating copies are safe) and the weights
-            // through L2 (other blocks rewrote them), eight loads in flight per
-            // thread
+            // the whole launch, so L1-allocating copies are safe) and the
+            // weights through L2 (other blocks rewrote them), eight loads in
+            // flight per thread
             __syncthreads();
             int64_t cs = r0;
             int cn = (int)min((int64_t)CAP, r1 - cs);
@@ -141,82 +139,16 @@ __global__ void __launch_bounds__(FNT, 1) k_fused_train(FArgs a) {
 #pragma unroll
                 for (int r = 0; r < 8; ++r) {
                     const int i = base + r * FNT + tid;
-                    if (i < HD) {
-                        const int j = i / D, k = i - j * D;
-                        Ws[j * WSTR + k] = v[r];
-                    } else if (i < P) {
-                        Bs[i - HD] = v[r];
-                    }
+                    if (i < P) Wm[i] = v[r];
                 }
             }
             cp_async_wait_all();
             __syncthreads();
-            float w[UPL][DP], b1r[UPL], w2r[UPL];
-#pragma unroll
-            for (int u = 0; u < UPL; ++u) {
-                const int j = u * 32 + lane;
-#pragma unroll
-                for (int k = 0; k < DP; ++k) w[u][k] = (j < H && k < D) ? Ws[j * WSTR + k] : 0.f;
-                b1r[u] = (j < H) ? Bs[j] : 0.f;
-                w2r[u] = (j < H) ? Bs[H + j] : 0.f;
-            }
-            const float b2 = Bs[2 * H];
-
-            float acc[UPL][DP], gb1a[UPL], gw2a[UPL], gb2a = 0.f;
-            double sse = 0.0;
-#pragma unroll
-            for (int u = 0; u < UPL; ++u) {
-                gb1a[u] = 0.f;
-                gw2a[u] = 0.f;
-#pragma unroll
-                for (int k = 0; k < DP; ++k) acc[u][k] = 0.f;
-            }
+            eng.load_weights(Wm);
 
             // ---- forward + backward over this block's rows of the step
             while (cn > 0) {
-                for (int s = warp; s < cn; s += FNW) {
-                    const float4 *xr = reinterpret_cast<const float4 *>(Xs + s * DP);
-                    float z[UPL];
-#pragma unroll
-                    for (int u = 0; u < UPL; ++u) z[u] = b1r[u];
-#pragma unroll
-                    for (int q = 0; q < DP / 4; ++q) {
-                        const float4 xv = xr[q];
-#pragma unroll
-                        for (int u = 0; u < UPL; ++u) {
-                            z[u] = fmaf(xv.x, w[u][4 * q + 0], z[u]);
-                            z[u] = fmaf(xv.y, w[u][4 * q + 1], z[u]);
-                            z[u] = fmaf(xv.z, w[u][4 * q + 2], z[u]);
-                            z[u] = fmaf(xv.w, w[u][4 * q + 3], z[u]);
-                        }
-                    }
-                    float hv[UPL], zp = 0.f;
-#pragma unroll
-                    for (int u = 0; u < UPL; ++u) {
-                        hv[u] = Act<ACT>::f(z[u]);
-                        zp = fmaf(hv[u], w2r[u], zp);
-                    }
-                    zp = warp_sum(zp);
-                    const float o = sigmoid_out(zp + b2);
-                    const float err = o - ys[s];
-                    const float d2 = c * err * o * (1.0f - o);
-                    sse += (double)err * (double)err;
-                    gb2a += d2;
-#pragma unroll
-                    for (int u = 0; u < UPL; ++u) {
-                        gw2a[u] = fmaf(d2, hv[u], gw2a[u]);
-                        const float d1 = d2 * w2r[u] * Act<ACT>::df(hv[u]);
-                        gb1a[u] += d1;
-#pragma unroll
-                        for (int q = 0; q < DP / 4; ++q) {
-                            const float4 xv = xr[q];
-                            acc[u][4 * q + 0] = fmaf(d1, xv.x, acc[u][4 * q + 0]);
-                            acc[u][4 * q + 1] = fmaf(d1, xv.y, acc[u][4 * q + 1]);
-                            acc[u][4 * q + 2] = fmaf(d1, xv.z, acc[u][4 * q + 2]);
-                            acc[u][4 * q + 3] = fmaf(d1, xv.w, acc[u][4 * q + 3]);
-                        }
-                    }
-                }
+                eng.rows(Xs, ys, cn, c, zx);
                 cs += cn;
                 cn = (int)min((int64_t)CAP, r1 - cs);
                 if (cn > 0) {
@@ -232,43 +164,27 @@ __global__ void __launch_bounds__(FNT, 1) k_fused_train(FArgs a) {
                 }
             }
 
-            // ---- block partial: warp partials summed in warp order
-            __syncthreads();
-            float *pw = parts + warp * P;
-#pragma unroll
-            for (int u = 0; u < UPL; ++u) {
-                const int j = u * 32 + lane;
-                if (j < H) {
-#pragma unroll
-                    for (int k = 0; k < DP; ++k)
-                        if (k < D) pw[j * D + k] = acc[u][k];
-                    pw[HD + j] = gb1a[u];
-                    pw[HD + H + j] = gw2a[u];
-                }
-            }
-            if (lane == 0) {
-                pw[P - 1] = gb2a;
-                s_red[warp] = sse;
-            }
+            // ---- block partial: row-group partials summed in group order
+            eng.write_group(gpart, s_red);
             __syncthreads();
             float *pg = part + (int64_t)g * P;
             for (int p = tid; p < P; p += FNT) {
-                float s = parts[p];
+                float s = gpart[p];
 #pragma unroll
-                for (int q = 1; q < FNW; ++q) s += parts[q * P + p];
+                for (int q = 1; q < NG; ++q) s += gpart[q * P + p];
                 pg[p] = s;
             }
             if (tid == 0) {
                 double t = 0.0;
-                for (int q = 0; q < FNW; ++q) t += s_red[q];
+                for (int q = 0; q < NG; ++q) t += s_red[q];
                 a.lossp[g] = t;
             }
             if (!grid_barrier(a.bar, (++nbar) * (unsigned)G, a.status)) return;
 
             // ---- cross-block reduction in a fixed order, update, norm partial
             double gn = 0.0;
-            const int64_t gw = (int64_t)g * FNW + warp;
-            for (int64_t p0 = gw * PPW; p0 < P; p0 += (int64_t)G * FNW * PPW) {
+            const int64_t gw = (int64_t)g * RE_NW + warp;
+            for (int64_t p0 = gw * PPW; p0 < P; p0 += (int64_t)G * RE_NW * PPW) {
                 float v[PPW][QMAX];
 #pragma unroll
                 for (int i = 0; i < PPW; ++i)
@@ -292,31 +208,58 @@ __global__ void __launch_bounds__(FNT, 1) k_fused_train(FArgs a) {
                     }
                 }
             }
+            __syncthreads();
             if (lane == 0) s_red[warp] = gn;
             __syncthreads();
             if (tid == 0) {
                 double t = 0.0;
-                for (int q = 0; q < FNW; ++q) t += s_red[q];
+                for (int q = 0; q < RE_NW; ++q) t += s_red[q];
                 a.gnp[g] = t;
             }
-            if (g == 0 && warp == 0) sse_epoch += fixed_sum(a.lossp, G, lane);
-            if (!grid_barrier(a.bar, (++nbar) * (unsigned)G, a.status)) return;
-            if (g == 0 && warp == 0) gn_last = fixed_sum(a.gnp, G, lane);
-        }
-        if (g == 0 && tid == 0) {
-            const double C = a.loss_mean ? (a.n > 0 ? 1.0 / (double)a.n : 0.0) : 1.0;
-            const double L = 0.5 * sse_epoch * C;
-            if (a.loss_hist) a.loss_hist[e] = L;
-            if (a.gnorm_hist) a.gnorm_hist[e] = sqrt(gn_last);
-            if (!isfinite(L)) atomicOr(a.status, ST_NONFINITE);
+            if (g == 0 && warp == 0) {
+                sse_epoch += fixed_sum(a.lossp, G, lane);
+                if (last_step && lane == 0) *a.epoch_sse = sse_epoch;
+            }
+            if (!last_step) {
+                if (!grid_barrier(a.bar, (++nbar) * (unsigned)G, a.status)) return;
+                if (g == 0 && warp == 0) gn_last = fixed_sum(a.gnp, G, lane);
+            } else {
+                // Last block to finish folds the loss and norm partials.
+                __syncthreads();
+                if (tid == 0) {
+                    __threadfence();
+                    s_last = (atomicAdd(a.bar + 1, 1u) == (unsigned)G - 1);
+                    __threadfence();
+                }
+                __syncthreads();
+                if (!s_last) return;
+                if (warp == 0) {
+                    gn_last = fixed_sum(a.gnp, G, lane);
+                    sse_epoch = __ldcg(a.epoch_sse);
+                }
+            }
+            if (b0 + mbs >= a.n && tid == 0 && (last_step || g == 0)) {
+                const double C = a.loss_mean ? (a.n > 0 ? 1.0 / (double)a.n : 0.0) : 1.0;
+                const double L = 0.5 * sse_epoch * C;
+                if (a.loss_hist) a.loss_hist[e] = L;
+                if (a.gnorm_hist) a.gnorm_hist[e] = sqrt(gn_last);
+                if (!isfinite(L)) atomicOr(a.status, ST_NONFINITE);
+            }
         }
     }
 }
 
-template <int DP, int UPL>
-void *pick_kernel(int act) {
-    if (act == MLP_ACT_TANH) return (void *)k_fused_train<DP, UPL, MLP_ACT_TANH>;
-    return (void *)k_fused_train<DP, UPL, MLP_ACT_SIGMOID>;
+template <int DP>
+void *pick_kernel(int act, int H) {
+    const int wu = re_wu(H);
+    if (act == MLP_ACT_TANH) {
+        if (wu == 1) return (void *)k_fused_train<DP, 1, MLP_ACT_TANH>;
+        if (wu == 2) return (void *)k_fused_train<DP, 2, MLP_ACT_TANH>;
+        return (void *)k_fused_train<DP, 4, MLP_ACT_TANH>;
+    }
+    if (wu == 1) return (void *)k_fused_train<DP, 1, MLP_ACT_SIGMOID>;
+    if (wu == 2) return (void *)k_fused_train<DP, 2, MLP_ACT_SIGMOID>;
+    return (void *)k_fused_train<DP, 4, MLP_ACT_SIGMOID>;
 }
 
 struct Choice {
@@ -325,29 +268,13 @@ struct Choice {
 };
 
 bool choose(int act, int D, int H, Choice *c) {
-    if (D < 1 || H < 1) return false;
-    if (D <= 8) {
-        if (H <= 32) *c = {pick_kernel<8, 1>(act), smem_bytes<8>(D, H)};
-        else if (H <= 64) *c = {pick_kernel<8, 2>(act), smem_bytes<8>(D, H)};
-        else return false;
-    } else if (D <= 16) {
-        if (H <= 32) *c = {pick_kernel<16, 1>(act), smem_bytes<16>(D, H)};
-        else if (H <= 64) *c = {pick_kernel<16, 2>(act), smem_bytes<16>(D, H)};
-        else return false;
-    } else if (D <= 36) {
-        if (H <= 32) *c = {pick_kernel<36, 1>(act), smem_bytes<36>(D, H)};
-        else if (H <= 64) *c = {pick_kernel<36, 2>(act), smem_bytes<36>(D, H)};
-        else return false;
-    } else if (D <= 48) {
-        if (H <= 32) *c = {pick_kernel<48, 1>(act), smem_bytes<48>(D, H)};
-        else if (H <= 64) *c = {pick_kernel<48, 2>(act), smem_bytes<48>(D, H)};
-        else return false;
-    } else if (D <= 64) {
-        if (H <= 32) *c = {pick_kernel<64, 1>(act), smem_bytes<64>(D, H)};
-        else return false;
-    } else {
-        return false;
-    }
+    if (D < 1 || H < 1 || H > 128) return false;
+    if (D <= 8) *c = {pick_kernel<8>(act, H), smem_bytes<8>(D, H)};
+    else if (D <= 16) *c = {pick_kernel<16>(act, H), smem_bytes<16>(D, H)};
+    else if (D <= 36) *c = {pick_kernel<36>(act, H), smem_bytes<36>(D, H)};
+    else if (D <= 48) *c = {pick_kernel<48>(act, H), smem_bytes<48>(D, H)};
+    else if (D <= 64) *c = {pick_kernel<64>(act, H), smem_bytes<64>(D, H)};
+    else return false;
     return true;
 }
 
@@ -408,6 +335,8 @@ void fused_scratch_carve(void *base, int D, int H, int sms, FusedScratch *s) {
     off = al(off + sizeof(double) * GMAX);
     s->gnp = (double *)(b + off);
     off = al(off + sizeof(double) * GMAX);
+    s->epoch_sse = (double *)(b + off);
+    off = al(off + sizeof(double));
     s->bar = (unsigned *)(b + off);
 }
 
@@ -435,7 +364,7 @@ cudaError_t fused_train(int act, int D, int H, int64_t n, const float *X, const 
     if (max_epochs < 1) return cudaErrorInvalidValue;
     for (int e0 = 0; e0 < epochs; e0 += (int)max_epochs) {
         int ne = (int)((epochs - e0) < max_epochs ? (epochs - e0) : max_epochs);
-        e = cudaMemsetAsync(s.bar, 0, sizeof(unsigned), st);
+        e = cudaMemsetAsync(s.bar, 0, 2 * sizeof(unsigned), st);
         if (e != cudaSuccess) return e;
         FArgs a;
         a.D = D;
@@ -454,6 +383,7 @@ cudaError_t fused_train(int act, int D, int H, int64_t n, const float *X, const 
         a.part = s.part;
         a.lossp = s.lossp;
         a.gnp = s.gnp;
+        a.epoch_sse = s.epoch_sse;
         a.bar = s.bar;
         a.skip_block = skip_block;
         void *args[] = {&a};

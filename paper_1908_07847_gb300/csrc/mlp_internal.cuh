@@ -169,10 +169,11 @@ cudaError_t plain_labels(int prec, int64_t n, const void *o, int8_t *labels, cud
 // ------------------------------------------------------- fused-path launcher
 
 struct FusedScratch {
-    float *part;     // G x P
-    double *lossp;   // G
-    double *gnp;     // G
-    unsigned *bar;   // 1
+    float *part;        // G x P
+    double *lossp;      // G
+    double *gnp;        // G
+    double *epoch_sse;  // 1
+    unsigned *bar;      // 2
 };
 
 // True if the fused cooperative kernel supports this shape.
