@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c1", choices=["c1", "c2"],
+                    help="c1: the 33-64-1 full-batch workload (default line); "
+                         "c2: 4096 independent 33-H-1 nets, 500 epochs per step")
     return ap.parse_args()
 
 
@@ -329,6 +332,96 @@ def run_reference(args, rank, world):
     print(json.dumps(out), flush=True)
 
 
+# ------------------------------------------------- many-nets workload (c2) --
+
+C2_NETS, C2_EPOCHS = 4096, 500
+C2_WORKLOAD = ("4096 independent 33-H-1 sigmoid MLPs, H ~ U{4..128}, n ~ U{50..120}, "
+               "full-batch GD lr 0.1, 500 epochs per step in one launch, FP32")
+
+
+def c2_inputs(rank: int):
+    from paper_1908_07847_gb300 import inputs as I
+    Hs, ns = I.batched_shapes(2 + rank, C2_NETS, (4, 128), (50, 120))
+    nets = []
+    for t in range(C2_NETS):
+        X = I.features(I.subseed(2 + rank, 100 + t), int(ns[t]), D_IN)
+        W = I.init_weights(I.subseed(2 + rank, 200 + t), D_IN, int(Hs[t]))
+        nets.append((X, W))
+    return Hs, ns, nets
+
+
+def run_c2(args, rank, world, local):
+    import torch
+    from paper_1908_07847_gb300 import binding as B
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream().cuda_stream
+    Hs, ns, nets = c2_inputs(rank)
+    _, _, T = workload_inputs(rank)
+    Xall = torch.from_numpy(np.concatenate([X for X, _ in nets])).to(dev)
+    th = B.mlp_create(D_IN, T[0].shape[0], LR, 1, B.MLP_FP32, B.MLP_ACT_SIGMOID)
+    B.mlp_set_weights(th, *T)
+    lab = torch.zeros(Xall.shape[0], dtype=torch.int8, device=dev)
+    B.mlp_predict(th, Xall, Xall.shape[0], lab, stream)
+    B.mlp_destroy(th)
+    yall = lab.to(torch.float32)
+    P0 = torch.from_numpy(np.concatenate([np.concatenate([W[0].ravel(), W[1], W[2], W[3]]) for _, W in nets])).to(dev)
+    Pw = P0.clone()
+    offs_x = np.concatenate([[0], np.cumsum(ns)[:-1]])
+    offs_p = np.concatenate([[0], np.cumsum((D_IN + 2) * Hs + 1)[:-1]])
+    descs = [B.mlp_net_desc(int(Hs[t]), int(ns[t]), Xall[int(offs_x[t]):].data_ptr(),
+                            yall[int(offs_x[t]):].data_ptr(), Pw[int(offs_p[t]):].data_ptr(), None)
+             for t in range(C2_NETS)]
+    plan = B.mlp_batch_create(B.MLP_FP32, B.MLP_ACT_SIGMOID, D_IN, descs, LR, 1)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    # one step = the whole 500-epoch launch, captured once in a CUDA graph
+    g = torch.cuda.CUDAGraph()
+    s2 = torch.cuda.Stream()
+    s2.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s2):
+        B.mlp_batch_run(plan, C2_EPOCHS, s2.cuda_stream)   # warm-up outside capture
+        s2.synchronize()
+        with torch.cuda.graph(g, stream=s2):
+            B.mlp_batch_run(plan, C2_EPOCHS, s2.cuda_stream)
+    torch.cuda.current_stream().wait_stream(s2)
+    for _ in range(max(args.warmup, 1)):
+        Pw.copy_(P0)
+        g.replay()
+    torch.cuda.synchronize()
+    steps = args.steps
+    times = []
+    with ClockSampler(local) as clk:
+        for _ in range(steps):
+            Pw.copy_(P0)
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            g.replay()
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1) * 1e-3)
+    assert B.mlp_batch_check(plan, stream) == B.MLP_OK, B.mlp_last_error()
+    B.mlp_batch_destroy(plan)
+    T_f = aggregate_max(sum(times), world)
+    units = int(ns.sum()) * C2_EPOCHS * world
+    flops = float(np.sum(ns * (4 * D_IN * Hs + 10 * Hs))) * C2_EPOCHS
+    peak = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    launch_s = statistics.mean(times)
+    out = {
+        "metric": METRIC, "value": units * steps / T_f, "unit": "sample-steps/s", "n_gpus": world,
+        "steps": steps, "warmup": args.warmup, "ms_per_step": T_f / steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": C2_WORKLOAD, "nets": C2_NETS, "rows_total": int(ns.sum()), "epochs_per_step": C2_EPOCHS,
+                   "l2": "flushed between timed steps (256 MiB write, outside the timed intervals)"},
+        "roofline": {"bound": "alu", "achieved": flops / launch_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+                     "frac": flops / launch_s / 1e12 / peak, "traffic": None, "kernel": "k_batched_train<36,sigmoid>",
+                     "flops_per_launch": flops},
+        "gpu_launches": steps, "clocks": clk.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -339,6 +432,8 @@ def main():
         dist.init_process_group("nccl")
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload == "c2":
+        run_c2(args, rank, world, local)
     else:
         run_ours(args, rank, world, local)
     if world > 1 and args.impl == "ours":

@@ -39,7 +39,9 @@
  *     message of the last failure on the calling thread is in mlp_last_error().
  *   - Kernels that wait on one another across thread blocks give up after about
  *     one second; they then record MLP_ETIMEOUT in the handle's device status,
- *     which mlp_check() returns.  Non-finite losses record MLP_ENONFINITE.
+ *     which mlp_check() returns.  Until mlp_check() has read it, further fused
+ *     training launches on that handle return without doing anything.
+ *     Non-finite losses record MLP_ENONFINITE.
  *   - n = 0 is valid: outputs of size n are untouched, gradients are zero,
  *     an update with zero gradients leaves the weights unchanged.
  */

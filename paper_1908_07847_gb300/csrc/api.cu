@@ -308,10 +308,14 @@ mlp_status mlp_train_epochs(mlp_t h, const void *X, const void *y, int64_t n, in
     }
     const int D = h->cfg.D, H = h->cfg.H;
     if (h->cfg.prec == MLP_FP32 && mlp::fused_supported(D, H)) {
+        void *before = h->fs;
         mlp_status s = grow(&h->fs, &h->fs_cap, mlp::fused_scratch_bytes(D, H, h->sms), "fused scratch");
         if (s) return s;
         mlp::FusedScratch fsc;
         mlp::fused_scratch_carve(h->fs, D, H, h->sms, &fsc);
+        // The kernel keeps its barrier counters at zero between launches; a
+        // fresh buffer starts them there.
+        if (h->fs != before) CK(cudaMemsetAsync(fsc.bar, 0, 2 * sizeof(unsigned), st), "fused scratch reset");
         CK(mlp::fused_train(h->cfg.act, D, H, n, (const float *)X, (const float *)y, (float *)h->params,
                             h->cfg.lr, h->cfg.loss_mean, epochs, minibatch, loss_hist, gnorm_hist, h->status,
                             fsc, h->rows_per_block, h->skip_block, st, nullptr),
@@ -392,7 +396,15 @@ mlp_status mlp_check(mlp_t h, void *stream) {
     int st = 0;
     CK(cudaMemcpy(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost), "mlp_check read");
     CK(cudaMemset(h->status, 0, sizeof(int)), "mlp_check clear");
-    if (st & mlp::ST_TIMEOUT) return fail(MLP_ETIMEOUT, "a cross-block wait gave up");
+    if (st & mlp::ST_TIMEOUT) {
+        // The failed launch left its barrier counters part-way: restart them.
+        if (h->fs) {
+            mlp::FusedScratch fsc;
+            mlp::fused_scratch_carve(h->fs, h->cfg.D, h->cfg.H, h->sms, &fsc);
+            CK(cudaMemset(fsc.bar, 0, 2 * sizeof(unsigned)), "mlp_check reset");
+        }
+        return fail(MLP_ETIMEOUT, "a cross-block wait gave up");
+    }
     if (st & mlp::ST_NONFINITE) return fail(MLP_ENONFINITE, "a loss was not finite");
     return MLP_OK;
 }

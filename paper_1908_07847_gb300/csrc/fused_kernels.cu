@@ -29,7 +29,7 @@ constexpr int FNT = RE_NT;       // threads per block
 constexpr int CAP = 64;          // rows staged in shared memory at a time
 constexpr int QMAX = 5;          // blocks per lane in the cross-block sums
 constexpr int GMAX = 32 * QMAX;  // largest grid
-constexpr int PPW = 4;           // parameters per warp per round
+constexpr int PPW = 8;           // parameters per warp per round
 
 struct FArgs {
     int D, H;
@@ -92,6 +92,9 @@ __global__ void __launch_bounds__(FNT, 1) k_fused_train(FArgs a) {
     float *zx = ys + CAP;                           // z2 exchange
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int G = gridDim.x, g = blockIdx.x;
+    // A launch after a failed one does nothing until the failure has been read
+    // (the host then also resets the counters).
+    if (ld_volatile(a.status) & ST_TIMEOUT) return;
     if (g == a.skip_block) return;                  // fault-injection hook (tests only)
     unsigned nbar = 0;
     const float *__restrict__ X = a.X;
@@ -129,18 +132,10 @@ __global__ void __launch_bounds__(FNT, 1) k_fused_train(FArgs a) {
                 }
                 for (int i = tid; i < cn; i += FNT) cp_async4(ys + i, Y + cs + i);
             }
-            for (int base = 0; base < P; base += 8 * FNT) {
-                float v[8];
-#pragma unroll
-                for (int r = 0; r < 8; ++r) {
-                    const int i = base + r * FNT + tid;
-                    v[r] = (i < P) ? __ldcg(params + i) : 0.f;
-                }
-#pragma unroll
-                for (int r = 0; r < 8; ++r) {
-                    const int i = base + r * FNT + tid;
-                    if (i < P) Wm[i] = v[r];
-                }
+            {
+                const int P4 = P & ~3;  // 16-byte copies through L2, then the tail
+                for (int i = 4 * tid; i < P4; i += 4 * FNT) cp_async16_cg(Wm + i, params + i);
+                if (tid < P - P4) Wm[P4 + tid] = __ldcg(params + P4 + tid);
             }
             cp_async_wait_all();
             __syncthreads();
@@ -236,6 +231,13 @@ __global__ void __launch_bounds__(FNT, 1) k_fused_train(FArgs a) {
                 if (warp == 0) {
                     gn_last = fixed_sum(a.gnp, G, lane);
                     sse_epoch = __ldcg(a.epoch_sse);
+                }
+                // Every other block has passed its last barrier and taken its
+                // ticket: reset both counters for the next launch.
+                if (tid == 0) {
+                    a.bar[0] = 0u;
+                    a.bar[1] = 0u;
+                    __threadfence();
                 }
             }
             if (b0 + mbs >= a.n && tid == 0 && (last_step || g == 0)) {
@@ -364,8 +366,6 @@ cudaError_t fused_train(int act, int D, int H, int64_t n, const float *X, const 
     if (max_epochs < 1) return cudaErrorInvalidValue;
     for (int e0 = 0; e0 < epochs; e0 += (int)max_epochs) {
         int ne = (int)((epochs - e0) < max_epochs ? (epochs - e0) : max_epochs);
-        e = cudaMemsetAsync(s.bar, 0, 2 * sizeof(unsigned), st);
-        if (e != cudaSuccess) return e;
         FArgs a;
         a.D = D;
         a.H = H;

@@ -76,6 +76,12 @@ __device__ __forceinline__ void cp_async4(void *smem_dst, const void *gmem_src) 
     unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem_src) : "memory");
 }
+// 16-byte asynchronous global -> shared copy that bypasses L1 (both addresses
+// 16-byte aligned).
+__device__ __forceinline__ void cp_async16_cg(void *smem_dst, const void *gmem_src) {
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem_src) : "memory");
+}
 __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
@@ -87,8 +93,8 @@ template <typename T> __device__ __forceinline__ T warp_sum(T v) {
 }
 
 // Grid-wide barrier for kernels launched cooperatively (all blocks resident).
-// `bar` counts arrivals monotonically from 0 (the host zeroes it before the
-// launch); the k-th barrier of the launch waits until it reaches k * nblocks.
+// `bar` counts arrivals monotonically from 0 (zero at the start of a launch);
+// the k-th barrier of the launch waits until it reaches k * nblocks.
 // The wait gives up after WAIT_LIMIT_NS, or as soon as another block has
 // recorded a failure, and then returns false after recording ST_TIMEOUT.
 __device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned target, int *status) {

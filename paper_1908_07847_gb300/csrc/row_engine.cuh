@@ -80,6 +80,9 @@ struct RowEngine {
         const int grp = warp / WU, wu = warp % WU;
         const int slot = lane / S;
         const int RPI = (32 / S) * RE_RB;
+        // Squared errors of this call are summed in FP32 per lane and folded
+        // into the FP64 sum once (FP64 arithmetic is slow on this part).
+        float sse_f = 0.f;
         for (int base = grp * RPI + slot * RE_RB; base < cn + slot * RE_RB; base += NG * RPI) {
             int xo[RE_RB];
             bool valid[RE_RB];
@@ -135,7 +138,7 @@ struct RowEngine {
                 const float o = sigmoid_out(zp[t] + b2);
                 const float err = o - ys[valid[t] ? base + t : 0];
                 const float d2 = valid[t] ? c * err * o * (1.0f - o) : 0.f;
-                if (valid[t]) sse += (double)err * (double)err;
+                if (valid[t]) sse_f = fmaf(err, err, sse_f);
                 gb2a += d2;
                 gw2a = fmaf(d2, hv[t], gw2a);
                 const float d1 = d2 * w2r * Act<ACT>::df(hv[t]);
@@ -154,6 +157,7 @@ struct RowEngine {
                 }
             }
         }
+        sse += (double)sse_f;
     }
 
     // Sum the segments of each warp (fixed butterfly) and write this row group's
