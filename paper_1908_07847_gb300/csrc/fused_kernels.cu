@@ -77,7 +77,7 @@ __device__ __forceinline__ T fixed_sum(const T *__restrict__ v, int G, int lane)
 }
 
 template <int DP, int WU, int ACT>
-__global__ void __launch_bounds__(FNT, 1) k_fused_train(FArgs a) {
+__global__ void __launch_bounds__(FNT, 2) k_fused_train(FArgs a) {
     extern __shared__ __align__(16) float smem[];
     __shared__ double s_red[RE_NW];
     __shared__ int s_last;

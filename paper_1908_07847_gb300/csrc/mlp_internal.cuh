@@ -20,11 +20,38 @@ constexpr unsigned long long WAIT_LIMIT_NS = 1000000000ull;
 
 // ---------------------------------------------------------------- activations
 
+// Eq. 1, sigmoid(x) = 1 / (1 + e^-x), in FP32 from hardware approximations:
+//   t = 2^(-|x| log2 e) in (0, 1]: the product |x| log2 e is split into
+//     hi + lo (Cody and Waite's split-constant argument reduction, with the
+//     exact product error from one fused multiply-add), 2^-hi comes from the
+//     ex2.approx instruction and 2^-lo ~ 1 - lo ln 2 corrects it;
+//   r = 1 / (1 + t) from rcp.approx refined by one Newton-Raphson step;
+//   sigmoid(x) = r for x >= 0 and t r for x < 0 (so that nothing overflows).
+// Maximum relative error about 4e-7 (ex2.approx's error dominates); the tests
+// bound it against FP64.
+__device__ __forceinline__ float sigmoid_f32(float x) {
+    const float L2E_HI = 1.44269502162933349609375f;      // log2(e) rounded to float
+    const float L2E_LO = 1.925963033500011079e-8f;        // log2(e) - L2E_HI
+    const float LN2 = 0.693147180559945309f;
+    float a = fabsf(x);
+    a = a > 104.0f ? 104.0f : a;  // 2^-150 is already 0; NaN passes through
+    const float hi = a * L2E_HI;
+    const float lo = fmaf(a, L2E_LO, fmaf(a, L2E_HI, -hi));
+    float t;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(t) : "f"(-hi));
+    t = fmaf(t, -lo * LN2, t);
+    const float d = 1.0f + t;
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(d));
+    r = fmaf(r, fmaf(-d, r, 1.0f), r);
+    return x >= 0.0f ? r : t * r;
+}
+
 template <int ACT> struct Act;
 
 // Eq. 1 sigmoid; derivative through the value: s (1 - s).
 template <> struct Act<MLP_ACT_SIGMOID> {
-    static __device__ __forceinline__ float f(float x) { return 1.0f / (1.0f + expf(-x)); }
+    static __device__ __forceinline__ float f(float x) { return sigmoid_f32(x); }
     static __device__ __forceinline__ double f(double x) { return 1.0 / (1.0 + exp(-x)); }
     static __device__ __forceinline__ float df(float v) { return v * (1.0f - v); }
     static __device__ __forceinline__ double df(double v) { return v * (1.0 - v); }
@@ -38,7 +65,7 @@ template <> struct Act<MLP_ACT_TANH> {
     static __device__ __forceinline__ double df(double v) { return 1.0 - v * v; }
 };
 
-__device__ __forceinline__ float sigmoid_out(float x) { return 1.0f / (1.0f + expf(-x)); }
+__device__ __forceinline__ float sigmoid_out(float x) { return sigmoid_f32(x); }
 __device__ __forceinline__ double sigmoid_out(double x) { return 1.0 / (1.0 + exp(-x)); }
 
 // ------------------------------------------------------------- element loads

@@ -34,6 +34,9 @@ __host__ __device__ inline int re_groups(int H) { return RE_NW / re_wu(H); }
 template <int DP, int WU, int ACT>
 struct RowEngine {
     static constexpr int NG = RE_NW / WU;
+    // Rows in flight per lane: segments of a warp already take separate rows
+    // when H <= 32, so two per lane keep the register budget there.
+    static constexpr int RB = (WU == 1) ? 2 : RE_RB;
     // Per-lane state: the neuron's weights and gradient sums.
     float w[DP];
     float acc[DP];
@@ -79,25 +82,25 @@ struct RowEngine {
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
         const int grp = warp / WU, wu = warp % WU;
         const int slot = lane / S;
-        const int RPI = (32 / S) * RE_RB;
+        const int RPI = (32 / S) * RB;
         // Squared errors of this call are summed in FP32 per lane and folded
         // into the FP64 sum once (FP64 arithmetic is slow on this part).
         float sse_f = 0.f;
-        for (int base = grp * RPI + slot * RE_RB; base < cn + slot * RE_RB; base += NG * RPI) {
-            int xo[RE_RB];
-            bool valid[RE_RB];
+        for (int base = grp * RPI + slot * RB; base < cn + slot * RB; base += NG * RPI) {
+            int xo[RB];
+            bool valid[RB];
 #pragma unroll
-            for (int t = 0; t < RE_RB; ++t) {
+            for (int t = 0; t < RB; ++t) {
                 valid[t] = base + t < cn;
                 xo[t] = (valid[t] ? base + t : 0) * DP;
             }
-            float z[RE_RB];
+            float z[RB];
 #pragma unroll
-            for (int t = 0; t < RE_RB; ++t) z[t] = b1r;
+            for (int t = 0; t < RB; ++t) z[t] = b1r;
 #pragma unroll
             for (int q = 0; q < DP / 4; ++q) {
 #pragma unroll
-                for (int t = 0; t < RE_RB; ++t) {
+                for (int t = 0; t < RB; ++t) {
                     const float4 xv = *reinterpret_cast<const float4 *>(Xs + xo[t] + 4 * q);
                     z[t] = fmaf(xv.x, w[4 * q + 0], z[t]);
                     z[t] = fmaf(xv.y, w[4 * q + 1], z[t]);
@@ -108,33 +111,39 @@ struct RowEngine {
             // Re-read the rows from shared memory in the backward pass instead of
             // keeping RB x DP values live in registers.
             asm volatile("" ::: "memory");
-            float hv[RE_RB], zp[RE_RB];
+            float hv[RB], zp[RB];
 #pragma unroll
-            for (int t = 0; t < RE_RB; ++t) {
+            for (int t = 0; t < RB; ++t) {
                 hv[t] = Act<ACT>::f(z[t]);
                 zp[t] = hv[t] * w2r;
             }
+            // Butterfly over the segment, level by level so that the RB rows'
+            // shuffles overlap.
 #pragma unroll
-            for (int t = 0; t < RE_RB; ++t)
-                for (int off = S >> 1; off > 0; off >>= 1) zp[t] += __shfl_xor_sync(0xffffffffu, zp[t], off);
+            for (int off = 16; off > 0; off >>= 1) {
+                if (WU > 1 || off < S) {
+#pragma unroll
+                    for (int t = 0; t < RB; ++t) zp[t] += __shfl_xor_sync(0xffffffffu, zp[t], off);
+                }
+            }
             if (WU > 1) {
-                float *zg = zx + (par * NG + grp) * (WU * RE_RB);
+                float *zg = zx + (par * NG + grp) * (WU * RB);
                 if (lane == 0) {
 #pragma unroll
-                    for (int t = 0; t < RE_RB; ++t) zg[wu * RE_RB + t] = zp[t];
+                    for (int t = 0; t < RB; ++t) zg[wu * RB + t] = zp[t];
                 }
                 asm volatile("bar.sync %0, %1;" ::"r"(1 + grp), "r"(WU * 32) : "memory");
 #pragma unroll
-                for (int t = 0; t < RE_RB; ++t) {
+                for (int t = 0; t < RB; ++t) {
                     float v = zg[t];
 #pragma unroll
-                    for (int q = 1; q < WU; ++q) v += zg[q * RE_RB + t];
+                    for (int q = 1; q < WU; ++q) v += zg[q * RB + t];
                     zp[t] = v;
                 }
                 par ^= 1;
             }
 #pragma unroll
-            for (int t = 0; t < RE_RB; ++t) {
+            for (int t = 0; t < RB; ++t) {
                 const float o = sigmoid_out(zp[t] + b2);
                 const float err = o - ys[valid[t] ? base + t : 0];
                 const float d2 = valid[t] ? c * err * o * (1.0f - o) : 0.f;
@@ -148,7 +157,7 @@ struct RowEngine {
 #pragma unroll
             for (int q = 0; q < DP / 4; ++q) {
 #pragma unroll
-                for (int t = 0; t < RE_RB; ++t) {
+                for (int t = 0; t < RB; ++t) {
                     const float4 xv = *reinterpret_cast<const float4 *>(Xs + xo[t] + 4 * q);
                     acc[4 * q + 0] = fmaf(hv[t], xv.x, acc[4 * q + 0]);
                     acc[4 * q + 1] = fmaf(hv[t], xv.y, acc[4 * q + 1]);
@@ -164,13 +173,18 @@ struct RowEngine {
     // gradient sums to part[grp * P ...] (packed layout) and its squared-error
     // sum to s_sse[grp].  The caller synchronises the block afterwards.
     __device__ __forceinline__ void write_group(float *part, double *s_sse) {
-        for (int off = S; off < 32; off <<= 1) {
+        if (WU == 1) {
 #pragma unroll
-            for (int k = 0; k < DP; ++k) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], off);
-            gb1a += __shfl_xor_sync(0xffffffffu, gb1a, off);
-            gw2a += __shfl_xor_sync(0xffffffffu, gw2a, off);
-            gb2a += __shfl_xor_sync(0xffffffffu, gb2a, off);
-            sse += __shfl_xor_sync(0xffffffffu, sse, off);
+            for (int off = 4; off < 32; off <<= 1) {
+                if (off >= S) {
+#pragma unroll
+                    for (int k = 0; k < DP; ++k) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], off);
+                    gb1a += __shfl_xor_sync(0xffffffffu, gb1a, off);
+                    gw2a += __shfl_xor_sync(0xffffffffu, gw2a, off);
+                    gb2a += __shfl_xor_sync(0xffffffffu, gb2a, off);
+                    sse += __shfl_xor_sync(0xffffffffu, sse, off);
+                }
+            }
         }
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
         const int grp = warp / WU, wu = warp % WU;

@@ -280,3 +280,33 @@ def test_nonfinite_loss_is_reported():
         net.set(W)
         B.mlp_train_epochs(net.h, dev(X), dev(y), n, 1, 0, None, None, stream())
         assert net.check() == B.MLP_ENONFINITE
+
+
+def test_fp32_sigmoid_error_bound():
+    """Eq. 1 in FP32 on the GPU (hidden activations of a 1-1 layer with unit
+    weight) against the FP64 value: relative error <= 5e-7 over [-80, 80],
+    exact limits at +-inf, NaN propagates."""
+    from scipy.special import expit
+    t = torch()
+    x = np.concatenate([np.linspace(-80, 80, 400001), [0.0, -0.0, 1e-30, -1e-30, 1e-3, -1e-3, 103.9, -87.0]])
+    x = x.astype(np.float32)
+    n = x.size
+    W1 = t.ones((1, 1), device="cuda")
+    zero = t.zeros(1, device="cuda")
+    hid = t.zeros((n, 1), device="cuda")
+    o = t.zeros(n, device="cuda")
+    nb = B.mlp_workspace_bytes(B.MLP_FP32, 1, 1, n)
+    ws = t.empty(nb, dtype=t.uint8, device="cuda")
+    B.mlp_forward_w(B.MLP_FP32, B.MLP_ACT_SIGMOID, 1, 1, n, dev(x.reshape(n, 1)), W1, zero, zero, zero, hid, o, ws,
+                    nb, stream())
+    got = host(hid)[:, 0].astype(np.float64)
+    ref = expit(x.astype(np.float64))
+    assert np.max(np.abs(got - ref) / ref) <= 5e-7
+    assert np.all(host(o) == 0.5)
+    special = np.array([np.inf, -np.inf, np.nan], np.float32).reshape(3, 1)
+    h3 = t.zeros((3, 1), device="cuda")
+    o3 = t.zeros(3, device="cuda")
+    B.mlp_forward_w(B.MLP_FP32, B.MLP_ACT_SIGMOID, 1, 1, 3, dev(special), W1, zero, zero, zero, h3, o3, ws, nb,
+                    stream())
+    r = host(h3)[:, 0]
+    assert r[0] == 1.0 and r[1] == 0.0 and np.isnan(r[2])
