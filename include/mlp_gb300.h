@@ -177,7 +177,7 @@ mlp_status mlp_backward_w(int32_t prec, int32_t act, int32_t D, int32_t H, int64
  * records MLP_ETIMEOUT (read it with mlp_check).  -1 restores normal runs. */
 mlp_status mlp_debug_skip_block(mlp_t net, int32_t skip_block);
 
-/* Rows per block of the fused training kernel (tuning knob, default 64). */
+/* Rows per block of the fused training kernel (tuning knob, default 32). */
 mlp_status mlp_set_rows_per_block(mlp_t net, int32_t rows);
 
 /*

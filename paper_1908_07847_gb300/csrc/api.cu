@@ -34,7 +34,8 @@ struct mlp_net {
     double *lstage = nullptr;
     size_t lstage_cap = 0;
     int skip_block = -1;
-    int rows_per_block = 64;
+    int rows_per_block = 32;
+    mlp::FusedCounters ctr;   // fused-kernel counter values at the next launch
 };
 
 namespace {
@@ -313,12 +314,14 @@ mlp_status mlp_train_epochs(mlp_t h, const void *X, const void *y, int64_t n, in
         if (s) return s;
         mlp::FusedScratch fsc;
         mlp::fused_scratch_carve(h->fs, D, H, h->sms, &fsc);
-        // The kernel keeps its barrier counters at zero between launches; a
-        // fresh buffer starts them there.
-        if (h->fs != before) CK(cudaMemsetAsync(fsc.bar, 0, 2 * sizeof(unsigned), st), "fused scratch reset");
+        // A fresh buffer starts its counters at zero.
+        if (h->fs != before) {
+            CK(cudaMemsetAsync(fsc.bar, 0, 2 * sizeof(unsigned long long), st), "fused scratch reset");
+            h->ctr = mlp::FusedCounters();
+        }
         CK(mlp::fused_train(h->cfg.act, D, H, n, (const float *)X, (const float *)y, (float *)h->params,
                             h->cfg.lr, h->cfg.loss_mean, epochs, minibatch, loss_hist, gnorm_hist, h->status,
-                            fsc, h->rows_per_block, h->skip_block, st, nullptr),
+                            fsc, &h->ctr, h->rows_per_block, h->skip_block, st, nullptr),
            "fused training kernel");
         return MLP_OK;
     }
@@ -401,7 +404,8 @@ mlp_status mlp_check(mlp_t h, void *stream) {
         if (h->fs) {
             mlp::FusedScratch fsc;
             mlp::fused_scratch_carve(h->fs, h->cfg.D, h->cfg.H, h->sms, &fsc);
-            CK(cudaMemset(fsc.bar, 0, 2 * sizeof(unsigned)), "mlp_check reset");
+            CK(cudaMemset(fsc.bar, 0, 2 * sizeof(unsigned long long)), "mlp_check reset");
+            h->ctr = mlp::FusedCounters();
         }
         return fail(MLP_ETIMEOUT, "a cross-block wait gave up");
     }

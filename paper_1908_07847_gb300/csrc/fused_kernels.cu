@@ -8,15 +8,14 @@
 //      per lane and accumulates the gradient rows in registers; activations
 //      never leave the chip;
 //   2. row-group partials are summed in shared memory in group order and
-//      written as one partial per block;
+//      written as one partial per block, with the block's FP64 squared error;
 //   3. grid barrier; every warp then owns a few parameters: its lanes load the
 //      block partials of a parameter in parallel (lane q takes blocks q, q+32,
 //      ...), add them in that order and finish with a butterfly -- a fixed
 //      order, so results are bitwise reproducible -- and lane 0 applies
-//      w -= lr g and adds g^2 to an FP64 norm partial;
-//   4. grid barrier before the next step; after the launch's last step the
-//      last block to finish (arrival ticket) folds the FP64 loss and norm
-//      partials instead, so a one-step launch waits on one barrier only.
+//      w -= lr g.  Warp 0 of block 0 folds the loss partials in the same round.
+//   4. a second grid barrier only before another step.  The gradient norm, if
+//      asked for, is folded by the last block to finish (an arrival ticket).
 #include <mutex>
 
 #include "row_engine.cuh"
@@ -47,8 +46,9 @@ struct FArgs {
     float *part;
     double *lossp;
     double *gnp;
-    double *epoch_sse;
-    unsigned *bar;   // [0]: barrier arrivals, [1]: last-step finish tickets
+    unsigned long long *bar;        // [0] barrier arrivals, [1] finish tickets
+    unsigned long long bar_base;    // their values at launch
+    unsigned long long ticket_base;
     int skip_block;
 };
 
@@ -92,11 +92,11 @@ __global__ void __launch_bounds__(FNT, 2) k_fused_train(FArgs a) {
     float *zx = ys + CAP;                           // z2 exchange
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int G = gridDim.x, g = blockIdx.x;
-    // A launch after a failed one does nothing until the failure has been read
-    // (the host then also resets the counters).
-    if (ld_volatile(a.status) & ST_TIMEOUT) return;
+    // A launch after a failed one must not touch the counters; the status load
+    // is consumed only before the first barrier, so it overlaps the staging.
+    const int status0 = ld_volatile(a.status);
     if (g == a.skip_block) return;                  // fault-injection hook (tests only)
-    unsigned nbar = 0;
+    unsigned long long target = a.bar_base;
     const float *__restrict__ X = a.X;
     const float *__restrict__ Y = a.y;
     float *__restrict__ params = a.params;
@@ -107,20 +107,21 @@ __global__ void __launch_bounds__(FNT, 2) k_fused_train(FArgs a) {
     for (int i = tid; i < CAP * DP; i += FNT) Xs[i] = 0.f;
 
     const int64_t mbs = (a.mb <= 0 || a.mb >= a.n) ? a.n : a.mb;
-    double sse_epoch = 0.0, gn_last = 0.0;
+    const double Cl = a.loss_mean ? (a.n > 0 ? 1.0 / (double)a.n : 0.0) : 1.0;
+    double sse_epoch = 0.0;
 
     for (int e = 0; e < a.epochs; ++e) {
         sse_epoch = 0.0;
         for (int64_t b0 = 0; b0 < a.n; b0 += mbs) {
             const int64_t m = min(mbs, a.n - b0);
-            const bool last_step = (e == a.epochs - 1) && (b0 + mbs >= a.n);
+            const bool epoch_end = b0 + mbs >= a.n;
+            const bool last_step = (e == a.epochs - 1) && epoch_end;
             const float c = a.loss_mean ? 1.0f / (float)m : 1.0f;
             const int64_t r0 = b0 + (m * g) / G, r1 = b0 + (m * (g + 1)) / G;
 
             // ---- stage the first rows asynchronously (X and y are read-only for
             // the whole launch, so L1-allocating copies are safe) and the
-            // weights through L2 (other blocks rewrote them), eight loads in
-            // flight per thread
+            // weights with 16-byte copies through L2 (other blocks rewrote them)
             __syncthreads();
             int64_t cs = r0;
             int cn = (int)min((int64_t)CAP, r1 - cs);
@@ -133,7 +134,7 @@ __global__ void __launch_bounds__(FNT, 2) k_fused_train(FArgs a) {
                 for (int i = tid; i < cn; i += FNT) cp_async4(ys + i, Y + cs + i);
             }
             {
-                const int P4 = P & ~3;  // 16-byte copies through L2, then the tail
+                const int P4 = P & ~3;
                 for (int i = 4 * tid; i < P4; i += 4 * FNT) cp_async16_cg(Wm + i, params + i);
                 if (tid < P - P4) Wm[P4 + tid] = __ldcg(params + P4 + tid);
             }
@@ -174,10 +175,14 @@ __global__ void __launch_bounds__(FNT, 2) k_fused_train(FArgs a) {
                 for (int q = 0; q < NG; ++q) t += s_red[q];
                 a.lossp[g] = t;
             }
-            if (!grid_barrier(a.bar, (++nbar) * (unsigned)G, a.status)) return;
+            if (status0 & ST_TIMEOUT) return;
+            target += (unsigned long long)G;
+            if (!grid_barrier(a.bar, target, a.status)) return;
 
-            // ---- cross-block reduction in a fixed order, update, norm partial
+            // ---- cross-block reduction in a fixed order and update; block 0's
+            // warp 0 folds the loss partials in the same round of loads
             double gn = 0.0;
+            if (g == 0 && warp == 0) sse_epoch += fixed_sum(a.lossp, G, lane);
             const int64_t gw = (int64_t)g * RE_NW + warp;
             for (int64_t p0 = gw * PPW; p0 < P; p0 += (int64_t)G * RE_NW * PPW) {
                 float v[PPW][QMAX];
@@ -203,49 +208,42 @@ __global__ void __launch_bounds__(FNT, 2) k_fused_train(FArgs a) {
                     }
                 }
             }
-            __syncthreads();
-            if (lane == 0) s_red[warp] = gn;
-            __syncthreads();
-            if (tid == 0) {
-                double t = 0.0;
-                for (int q = 0; q < RE_NW; ++q) t += s_red[q];
-                a.gnp[g] = t;
+            if (epoch_end && g == 0 && tid == 0) {
+                const double L = 0.5 * sse_epoch * Cl;
+                if (a.loss_hist) a.loss_hist[e] = L;
+                if (!isfinite(L)) atomicOr(a.status, ST_NONFINITE);
             }
-            if (g == 0 && warp == 0) {
-                sse_epoch += fixed_sum(a.lossp, G, lane);
-                if (last_step && lane == 0) *a.epoch_sse = sse_epoch;
+            const bool want_gn = a.gnorm_hist && epoch_end;
+            if (want_gn) {
+                __syncthreads();
+                if (lane == 0) s_red[warp] = gn;
+                __syncthreads();
+                if (tid == 0) {
+                    double t = 0.0;
+                    for (int q = 0; q < RE_NW; ++q) t += s_red[q];
+                    a.gnp[g] = t;
+                }
             }
             if (!last_step) {
-                if (!grid_barrier(a.bar, (++nbar) * (unsigned)G, a.status)) return;
-                if (g == 0 && warp == 0) gn_last = fixed_sum(a.gnp, G, lane);
-            } else {
-                // Last block to finish folds the loss and norm partials.
+                target += (unsigned long long)G;
+                if (!grid_barrier(a.bar, target, a.status)) return;
+                if (want_gn && g == 0 && warp == 0) {
+                    const double t = fixed_sum(a.gnp, G, lane);
+                    if (lane == 0) a.gnorm_hist[e] = sqrt(t);
+                }
+            } else if (want_gn) {
+                // The last block to finish folds the norm partials.
                 __syncthreads();
                 if (tid == 0) {
                     __threadfence();
-                    s_last = (atomicAdd(a.bar + 1, 1u) == (unsigned)G - 1);
+                    s_last = (atomicAdd(a.bar + 1, 1ull) == a.ticket_base + (unsigned long long)G - 1);
                     __threadfence();
                 }
                 __syncthreads();
-                if (!s_last) return;
-                if (warp == 0) {
-                    gn_last = fixed_sum(a.gnp, G, lane);
-                    sse_epoch = __ldcg(a.epoch_sse);
+                if (s_last && warp == 0) {
+                    const double t = fixed_sum(a.gnp, G, lane);
+                    if (lane == 0) a.gnorm_hist[e] = sqrt(t);
                 }
-                // Every other block has passed its last barrier and taken its
-                // ticket: reset both counters for the next launch.
-                if (tid == 0) {
-                    a.bar[0] = 0u;
-                    a.bar[1] = 0u;
-                    __threadfence();
-                }
-            }
-            if (b0 + mbs >= a.n && tid == 0 && (last_step || g == 0)) {
-                const double C = a.loss_mean ? (a.n > 0 ? 1.0 / (double)a.n : 0.0) : 1.0;
-                const double L = 0.5 * sse_epoch * C;
-                if (a.loss_hist) a.loss_hist[e] = L;
-                if (a.gnorm_hist) a.gnorm_hist[e] = sqrt(gn_last);
-                if (!isfinite(L)) atomicOr(a.status, ST_NONFINITE);
             }
         }
     }
@@ -337,15 +335,13 @@ void fused_scratch_carve(void *base, int D, int H, int sms, FusedScratch *s) {
     off = al(off + sizeof(double) * GMAX);
     s->gnp = (double *)(b + off);
     off = al(off + sizeof(double) * GMAX);
-    s->epoch_sse = (double *)(b + off);
-    off = al(off + sizeof(double));
-    s->bar = (unsigned *)(b + off);
+    s->bar = (unsigned long long *)(b + off);
 }
 
 cudaError_t fused_train(int act, int D, int H, int64_t n, const float *X, const float *y, float *params,
                         float lr, int loss_mean, int epochs, int64_t mb, double *loss_hist, double *gnorm_hist,
-                        int *status, const FusedScratch &s, int rows_per_block, int skip_block,
-                        cudaStream_t st, int *grid_used) {
+                        int *status, const FusedScratch &s, FusedCounters *ctr, int rows_per_block,
+                        int skip_block, cudaStream_t st, int *grid_used) {
     Choice ch;
     if (!choose(act, D, H, &ch)) return cudaErrorInvalidValue;
     cudaError_t e;
@@ -354,42 +350,42 @@ cudaError_t fused_train(int act, int D, int H, int64_t n, const float *X, const 
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     const int sms = device_sm_count();
     const int64_t mbs = (mb <= 0 || mb >= n) ? n : mb;
-    if (rows_per_block < 1) rows_per_block = 64;
+    if (rows_per_block < 1) rows_per_block = 32;
     int64_t G = cdiv(mbs > 0 ? mbs : 1, rows_per_block);
     if (G > (int64_t)per_sm * sms) G = (int64_t)per_sm * sms;
     if (G > GMAX) G = GMAX;
     if (G < 1) G = 1;
     if (grid_used) *grid_used = (int)G;
-    const int64_t steps_per_epoch = n > 0 ? cdiv(n, mbs) : 0;
-    // Barrier targets are 32-bit: split the epochs over launches if needed.
-    int64_t max_epochs = steps_per_epoch > 0 ? (int64_t)(0x7fffffff / (2 * G * steps_per_epoch)) : epochs;
-    if (max_epochs < 1) return cudaErrorInvalidValue;
-    for (int e0 = 0; e0 < epochs; e0 += (int)max_epochs) {
-        int ne = (int)((epochs - e0) < max_epochs ? (epochs - e0) : max_epochs);
-        FArgs a;
-        a.D = D;
-        a.H = H;
-        a.n = n;
-        a.X = X;
-        a.y = y;
-        a.params = params;
-        a.lr = lr;
-        a.loss_mean = loss_mean;
-        a.epochs = ne;
-        a.mb = mb;
-        a.loss_hist = loss_hist ? loss_hist + e0 : nullptr;
-        a.gnorm_hist = gnorm_hist ? gnorm_hist + e0 : nullptr;
-        a.status = status;
-        a.part = s.part;
-        a.lossp = s.lossp;
-        a.gnp = s.gnp;
-        a.epoch_sse = s.epoch_sse;
-        a.bar = s.bar;
-        a.skip_block = skip_block;
-        void *args[] = {&a};
-        e = cudaLaunchCooperativeKernel(ch.fn, dim3((unsigned)G), dim3(FNT), args, ch.smem, st);
-        if (e != cudaSuccess) return e;
-    }
+    const int64_t steps = n > 0 ? cdiv(n, mbs) * (int64_t)epochs : 0;
+    if (steps == 0) return cudaSuccess;
+    FArgs a;
+    a.D = D;
+    a.H = H;
+    a.n = n;
+    a.X = X;
+    a.y = y;
+    a.params = params;
+    a.lr = lr;
+    a.loss_mean = loss_mean;
+    a.epochs = epochs;
+    a.mb = mb;
+    a.loss_hist = loss_hist;
+    a.gnorm_hist = gnorm_hist;
+    a.status = status;
+    a.part = s.part;
+    a.lossp = s.lossp;
+    a.gnp = s.gnp;
+    a.bar = s.bar;
+    a.bar_base = ctr->bar;
+    a.ticket_base = ctr->ticket;
+    a.skip_block = skip_block;
+    void *args[] = {&a};
+    e = cudaLaunchCooperativeKernel(ch.fn, dim3((unsigned)G), dim3(FNT), args, ch.smem, st);
+    if (e != cudaSuccess) return e;
+    // Every block arrives at 2 * steps - 1 barriers and, when the norm is
+    // folded at the end, takes one ticket.
+    ctr->bar += (unsigned long long)G * (unsigned long long)(2 * steps - 1);
+    if (gnorm_hist) ctr->ticket += (unsigned long long)G;
     return cudaSuccess;
 }
 

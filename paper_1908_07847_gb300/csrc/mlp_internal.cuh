@@ -87,9 +87,9 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
-__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
 
@@ -120,16 +120,18 @@ template <typename T> __device__ __forceinline__ T warp_sum(T v) {
 }
 
 // Grid-wide barrier for kernels launched cooperatively (all blocks resident).
-// `bar` counts arrivals monotonically from 0 (zero at the start of a launch);
-// the k-th barrier of the launch waits until it reaches k * nblocks.
-// The wait gives up after WAIT_LIMIT_NS, or as soon as another block has
-// recorded a failure, and then returns false after recording ST_TIMEOUT.
-__device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned target, int *status) {
+// `bar` is a 64-bit arrival counter that only ever grows; the host passes the
+// value it had when the launch started (it knows how many arrivals every
+// launch adds), and the k-th barrier of the launch waits until the counter
+// reaches base + k * nblocks.  The wait gives up after WAIT_LIMIT_NS, or as
+// soon as another block has recorded a failure, and then returns false after
+// recording ST_TIMEOUT.
+__device__ __forceinline__ bool grid_barrier(unsigned long long *bar, unsigned long long target, int *status) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        atomicAdd(bar, 1u);
+        atomicAdd(bar, 1ull);
         unsigned long long t0 = global_ns();
         int ok = 1;
         while (ld_acquire(bar) < target) {
@@ -202,11 +204,16 @@ cudaError_t plain_labels(int prec, int64_t n, const void *o, int8_t *labels, cud
 // ------------------------------------------------------- fused-path launcher
 
 struct FusedScratch {
-    float *part;        // G x P
-    double *lossp;      // G
-    double *gnp;        // G
-    double *epoch_sse;  // 1
-    unsigned *bar;      // 2
+    float *part;              // G x P
+    double *lossp;            // G
+    double *gnp;              // G
+    unsigned long long *bar;  // [0] barrier arrivals, [1] finish tickets
+};
+
+// Host-side view of the counters: their values when the next launch starts.
+struct FusedCounters {
+    unsigned long long bar = 0;
+    unsigned long long ticket = 0;
 };
 
 // True if the fused cooperative kernel supports this shape.
@@ -216,11 +223,12 @@ size_t fused_scratch_bytes(int D, int H, int sms);
 void fused_scratch_carve(void *base, int D, int H, int sms, FusedScratch *s);
 
 // Trains in place on the packed FP32 params [W1, b1, w2, b2].
+// `ctr` is advanced by the arrivals the launches add.
 cudaError_t fused_train(int act, int D, int H, int64_t n, const float *X, const float *y,
                         float *params, float lr, int loss_mean, int epochs, int64_t mb,
                         double *loss_hist, double *gnorm_hist, int *status,
-                        const FusedScratch &s, int rows_per_block, int skip_block,
-                        cudaStream_t st, int *grid_used);
+                        const FusedScratch &s, FusedCounters *ctr, int rows_per_block,
+                        int skip_block, cudaStream_t st, int *grid_used);
 
 // ------------------------------------------------------ batched-path launcher
 
