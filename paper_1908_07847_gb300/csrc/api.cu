@@ -314,9 +314,9 @@ mlp_status mlp_train_epochs(mlp_t h, const void *X, const void *y, int64_t n, in
         if (s) return s;
         mlp::FusedScratch fsc;
         mlp::fused_scratch_carve(h->fs, D, H, h->sms, &fsc);
-        // A fresh buffer starts its counters at zero.
+        // A fresh buffer starts with zero accumulators and counter.
         if (h->fs != before) {
-            CK(cudaMemsetAsync(fsc.bar, 0, 2 * sizeof(unsigned long long), st), "fused scratch reset");
+            CK(cudaMemsetAsync(h->fs, 0, h->fs_cap, st), "fused scratch reset");
             h->ctr = mlp::FusedCounters();
         }
         CK(mlp::fused_train(h->cfg.act, D, H, n, (const float *)X, (const float *)y, (float *)h->params,
@@ -402,9 +402,7 @@ mlp_status mlp_check(mlp_t h, void *stream) {
     if (st & mlp::ST_TIMEOUT) {
         // The failed launch left its barrier counters part-way: restart them.
         if (h->fs) {
-            mlp::FusedScratch fsc;
-            mlp::fused_scratch_carve(h->fs, h->cfg.D, h->cfg.H, h->sms, &fsc);
-            CK(cudaMemset(fsc.bar, 0, 2 * sizeof(unsigned long long)), "mlp_check reset");
+            CK(cudaMemset(h->fs, 0, h->fs_cap), "mlp_check reset");
             h->ctr = mlp::FusedCounters();
         }
         return fail(MLP_ETIMEOUT, "a cross-block wait gave up");

@@ -1,21 +1,26 @@
 // Fused training kernel for small networks (D <= 64, H <= 128): one cooperative
-// launch runs every step of every epoch.  Per step (Sec. 2.2 of arXiv
-// 1908.07847: feed-forward, output error, backpropagation, gradient descent
-// with no momentum):
-//   1. every block stages the packed weights (through L2: other blocks rewrote
-//      them) and its rows of X (asynchronous copies) in shared memory; the row
-//      engine (row_engine.cuh) runs forward and backward with one hidden neuron
-//      per lane and accumulates the gradient rows in registers; activations
-//      never leave the chip;
-//   2. row-group partials are summed in shared memory in group order and
-//      written as one partial per block, with the block's FP64 squared error;
-//   3. grid barrier; every warp then owns a few parameters: its lanes load the
-//      block partials of a parameter in parallel (lane q takes blocks q, q+32,
-//      ...), add them in that order and finish with a butterfly -- a fixed
-//      order, so results are bitwise reproducible -- and lane 0 applies
-//      w -= lr g.  Warp 0 of block 0 folds the loss partials in the same round.
-//   4. a second grid barrier only before another step.  The gradient norm, if
-//      asked for, is folded by the last block to finish (an arrival ticket).
+// launch runs every step of every epoch, with one grid barrier per step.
+//
+// Per step (Sec. 2.2 of arXiv 1908.07847: feed-forward, output error,
+// backpropagation, gradient descent with no momentum):
+//   1. every block holds a copy of the packed weights in shared memory and its
+//      rows of X (staged with asynchronous copies, kept there across epochs when
+//      they fit); the row engine (row_engine.cuh) runs forward and backward
+//      with one hidden neuron per lane and accumulates the gradient rows in
+//      registers; activations never leave the chip;
+//   2. the row groups' partial gradients are summed in shared memory in group
+//      order, converted to 64-bit fixed point (scale 2^E) and added into a
+//      global accumulator with integer atomics.  Integer addition does not
+//      depend on the order, so the cross-block sum is exact and bitwise
+//      reproducible; the block's squared error joins it the same way;
+//   3. one grid barrier; every block then reads the whole summed gradient,
+//      converts it back and applies w -= lr g to its own copy of the weights,
+//      so all copies stay identical and no second barrier is needed; block 0
+//      also records the epoch loss (and, if asked, the FP64 gradient norm);
+//   4. the accumulator is triple-buffered: while reading buffer s, each block
+//      clears its share of buffer s + 2, which the barrier of step s + 1 then
+//      publishes before anyone adds into it.
+// At the end block 0 writes its copy of the weights back.
 #include <mutex>
 
 #include "row_engine.cuh"
@@ -26,9 +31,8 @@ namespace {
 
 constexpr int FNT = RE_NT;       // threads per block
 constexpr int CAP = 64;          // rows staged in shared memory at a time
-constexpr int QMAX = 5;          // blocks per lane in the cross-block sums
-constexpr int GMAX = 32 * QMAX;  // largest grid
-constexpr int PPW = 8;           // parameters per warp per round
+constexpr int RESIDENT = 192;    // rows a block keeps resident across steps
+constexpr int GMAX = 320;        // largest grid
 
 struct FArgs {
     int D, H;
@@ -40,213 +44,176 @@ struct FArgs {
     int loss_mean;
     int epochs;
     int64_t mb;
+    int gshift;                     // fixed-point scale 2^gshift of the gradient
     double *loss_hist;
     double *gnorm_hist;
     int *status;
-    float *part;
-    double *lossp;
-    double *gnp;
-    unsigned long long *bar;        // [0] barrier arrivals, [1] finish tickets
-    unsigned long long bar_base;    // their values at launch
-    unsigned long long ticket_base;
+    long long *acc;                 // 3 x (P + 1) fixed-point accumulators
+    int rot;                        // buffer of the first step
+    unsigned long long *bar;        // barrier arrivals
+    unsigned long long bar_base;    // its value at launch
     int skip_block;
 };
 
-inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+__host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 // Shared-memory layout (floats): packed weights [P], row-group partials
-// [NG x P], CAP rows of X (DP wide, zero padded), CAP labels, z2 exchange.
+// [NG x P], rows of X (DP wide, zero padded), labels, z2 exchange.
 __host__ __device__ inline int wm_floats(int D, int H) { return ((D + 2) * H + 1 + 3) & ~3; }
 
 template <int DP>
-size_t smem_bytes(int D, int H) {
-    return sizeof(float) * ((size_t)wm_floats(D, H) + re_part_floats(D, H) + (size_t)CAP * DP + CAP + RE_ZX);
+size_t smem_bytes(int D, int H, int rows) {
+    return sizeof(float) * ((size_t)wm_floats(D, H) + re_part_floats(D, H) + (size_t)rows * DP + rows + RE_ZX);
 }
 
-// Sum of v[q] for q < G in a fixed order: lane l adds q = l, l+32, ... in turn,
-// then a butterfly over the lanes.  Every lane returns the same value.
-template <typename T>
-__device__ __forceinline__ T fixed_sum(const T *__restrict__ v, int G, int lane) {
-    T s = T(0);
-#pragma unroll
-    for (int t = 0; t < QMAX; ++t) {
-        const int q = lane + 32 * t;
-        if (q < G) s += __ldcg(v + q);
-    }
-    return warp_sum(s);
+__device__ __forceinline__ void red_add(long long *p, long long v) {
+    asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
 template <int DP, int WU, int ACT>
 __global__ void __launch_bounds__(FNT, 2) k_fused_train(FArgs a) {
     extern __shared__ __align__(16) float smem[];
     __shared__ double s_red[RE_NW];
-    __shared__ int s_last;
     using Eng = RowEngine<DP, WU, ACT>;
     constexpr int NG = Eng::NG;
     const int D = a.D, H = a.H;
     const int P = (D + 2) * H + 1;
-    float *Wm = smem;                               // packed weights
-    float *gpart = Wm + wm_floats(D, H);            // NG x P row-group partials
-    float *Xs = gpart + re_part_floats(D, H);       // CAP x DP rows
-    float *ys = Xs + CAP * DP;                      // CAP labels
-    float *zx = ys + CAP;                           // z2 exchange
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int P1 = P + 1;                           // + the squared error
+    const int tid = threadIdx.x;
     const int G = gridDim.x, g = blockIdx.x;
     // A launch after a failed one must not touch the counters; the status load
     // is consumed only before the first barrier, so it overlaps the staging.
     const int status0 = ld_volatile(a.status);
     if (g == a.skip_block) return;                  // fault-injection hook (tests only)
+
+    const int64_t mbs = (a.mb <= 0 || a.mb >= a.n) ? a.n : a.mb;
+    // Rows of a step per block, and whether they stay resident for the launch.
+    const int64_t rows_max = cdiv(mbs, G);
+    const bool resident = (mbs == a.n) && rows_max <= RESIDENT;
+    const int xcap = resident ? RESIDENT : CAP;
+    float *Wm = smem;                               // packed weights
+    float *gpart = Wm + wm_floats(D, H);            // NG x P row-group partials
+    float *Xs = gpart + re_part_floats(D, H);       // xcap x DP rows
+    float *ys = Xs + xcap * DP;                     // xcap labels
+    float *zx = ys + xcap;                          // z2 exchange
     unsigned long long target = a.bar_base;
     const float *__restrict__ X = a.X;
     const float *__restrict__ Y = a.y;
-    float *__restrict__ params = a.params;
-    float *__restrict__ part = a.part;
     Eng eng;
     eng.setup(H, D);
-
-    for (int i = tid; i < CAP * DP; i += FNT) Xs[i] = 0.f;
-
-    const int64_t mbs = (a.mb <= 0 || a.mb >= a.n) ? a.n : a.mb;
+    const float gscale = __int_as_float((127 - a.gshift) << 23);   // 2^-gshift
+    const float gup = __int_as_float((127 + a.gshift) << 23);      // 2^gshift
     const double Cl = a.loss_mean ? (a.n > 0 ? 1.0 / (double)a.n : 0.0) : 1.0;
-    double sse_epoch = 0.0;
 
+    for (int i = tid; i < xcap * DP; i += FNT) Xs[i] = 0.f;
+    __syncthreads();
+    {
+        // Initial weights: 16-byte copies through L2, then the tail.
+        const int P4 = P & ~3;
+        for (int i = 4 * tid; i < P4; i += 4 * FNT) cp_async16_cg(Wm + i, a.params + i);
+        if (tid < P - P4) Wm[P4 + tid] = __ldcg(a.params + P4 + tid);
+    }
+    auto stage = [&](int64_t r0, int cn) {
+        const float *Xg = X + r0 * D;
+        for (int i = tid; i < cn * D; i += FNT) {
+            const int s = i / D, k = i - s * D;
+            cp_async4(Xs + s * DP + k, Xg + i);
+        }
+        for (int i = tid; i < cn; i += FNT) cp_async4(ys + i, Y + r0 + i);
+    };
+    if (resident) {
+        const int64_t r0 = (mbs * g) / G, r1 = (mbs * (g + 1)) / G;
+        if (r1 > r0) stage(r0, (int)(r1 - r0));
+    }
+    cp_async_wait_all();
+    __syncthreads();
+
+    double sse_epoch = 0.0;
+    int64_t step = 0;
     for (int e = 0; e < a.epochs; ++e) {
         sse_epoch = 0.0;
-        for (int64_t b0 = 0; b0 < a.n; b0 += mbs) {
+        for (int64_t b0 = 0; b0 < a.n; b0 += mbs, ++step) {
             const int64_t m = min(mbs, a.n - b0);
             const bool epoch_end = b0 + mbs >= a.n;
-            const bool last_step = (e == a.epochs - 1) && epoch_end;
             const float c = a.loss_mean ? 1.0f / (float)m : 1.0f;
             const int64_t r0 = b0 + (m * g) / G, r1 = b0 + (m * (g + 1)) / G;
-
-            // ---- stage the first rows asynchronously (X and y are read-only for
-            // the whole launch, so L1-allocating copies are safe) and the
-            // weights with 16-byte copies through L2 (other blocks rewrote them)
-            __syncthreads();
-            int64_t cs = r0;
-            int cn = (int)min((int64_t)CAP, r1 - cs);
-            if (cn > 0) {
-                const float *Xg = X + cs * D;
-                for (int i = tid; i < cn * D; i += FNT) {
-                    const int s = i / D, k = i - s * D;
-                    cp_async4(Xs + s * DP + k, Xg + i);
-                }
-                for (int i = tid; i < cn; i += FNT) cp_async4(ys + i, Y + cs + i);
-            }
-            {
-                const int P4 = P & ~3;
-                for (int i = 4 * tid; i < P4; i += 4 * FNT) cp_async16_cg(Wm + i, params + i);
-                if (tid < P - P4) Wm[P4 + tid] = __ldcg(params + P4 + tid);
-            }
-            cp_async_wait_all();
-            __syncthreads();
-            eng.load_weights(Wm);
+            long long *acc = a.acc + (size_t)((a.rot + step) % 3) * P1;
+            long long *acc_clear = a.acc + (size_t)((a.rot + step + 2) % 3) * P1;
 
             // ---- forward + backward over this block's rows of the step
-            while (cn > 0) {
-                eng.rows(Xs, ys, cn, c, zx);
-                cs += cn;
-                cn = (int)min((int64_t)CAP, r1 - cs);
-                if (cn > 0) {
+            eng.load_weights(Wm);
+            if (resident) {
+                if (r1 > r0) eng.rows(Xs, ys, (int)(r1 - r0), c, zx);
+            } else {
+                for (int64_t cs = r0; cs < r1; cs += CAP) {
+                    const int cn = (int)min((int64_t)CAP, r1 - cs);
                     __syncthreads();
-                    const float *Xg = X + cs * D;
-                    for (int i = tid; i < cn * D; i += FNT) {
-                        const int s = i / D, k = i - s * D;
-                        cp_async4(Xs + s * DP + k, Xg + i);
-                    }
-                    for (int i = tid; i < cn; i += FNT) cp_async4(ys + i, Y + cs + i);
+                    stage(cs, cn);
                     cp_async_wait_all();
                     __syncthreads();
+                    eng.rows(Xs, ys, cn, c, zx);
                 }
             }
 
-            // ---- block partial: row-group partials summed in group order
+            // ---- block partial, in fixed point, into the global accumulator
             eng.write_group(gpart, s_red);
             __syncthreads();
-            float *pg = part + (int64_t)g * P;
+            int bad = 0;
             for (int p = tid; p < P; p += FNT) {
                 float s = gpart[p];
 #pragma unroll
                 for (int q = 1; q < NG; ++q) s += gpart[q * P + p];
-                pg[p] = s;
+                const float v = s * gup;
+                if (!(fabsf(v) < 4.0e18f)) bad = 1;   // out of range or NaN
+                red_add(acc + p, __float2ll_rn(v));
             }
             if (tid == 0) {
                 double t = 0.0;
                 for (int q = 0; q < NG; ++q) t += s_red[q];
-                a.lossp[g] = t;
+                const double v = t * 4294967296.0;
+                if (!(v < 4.0e18)) bad = 1;
+                red_add(acc + P, __double2ll_rn(v));
             }
+            if (bad) atomicOr(a.status, ST_NONFINITE);
             if (status0 & ST_TIMEOUT) return;
             target += (unsigned long long)G;
             if (!grid_barrier(a.bar, target, a.status)) return;
 
-            // ---- cross-block reduction in a fixed order and update; block 0's
-            // warp 0 folds the loss partials in the same round of loads
+            // ---- every block applies the summed gradient to its own copy
+            const bool want_gn = g == 0 && a.gnorm_hist && epoch_end;
             double gn = 0.0;
-            if (g == 0 && warp == 0) sse_epoch += fixed_sum(a.lossp, G, lane);
-            const int64_t gw = (int64_t)g * RE_NW + warp;
-            for (int64_t p0 = gw * PPW; p0 < P; p0 += (int64_t)G * RE_NW * PPW) {
-                float v[PPW][QMAX];
-#pragma unroll
-                for (int i = 0; i < PPW; ++i)
-#pragma unroll
-                    for (int t = 0; t < QMAX; ++t) {
-                        const int q = lane + 32 * t;
-                        v[i][t] = (q < G && p0 + i < P) ? __ldcg(part + (int64_t)q * P + p0 + i) : 0.f;
-                    }
-                float old[PPW];
-#pragma unroll
-                for (int i = 0; i < PPW; ++i) old[i] = (lane == 0 && p0 + i < P) ? __ldcg(params + p0 + i) : 0.f;
-#pragma unroll
-                for (int i = 0; i < PPW; ++i) {
-                    float s = v[i][0];
-#pragma unroll
-                    for (int t = 1; t < QMAX; ++t) s += v[i][t];
-                    s = warp_sum(s);
-                    if (lane == 0 && p0 + i < P) {
-                        params[p0 + i] = old[i] - a.lr * s;
-                        gn += (double)s * (double)s;
-                    }
+            for (int p = tid; p < P; p += FNT) {
+                const float gsum = (float)__ldcg(acc + p) * gscale;
+                Wm[p] -= a.lr * gsum;
+                if (want_gn) gn = fma((double)gsum, (double)gsum, gn);
+            }
+            for (int p = (int)(((int64_t)P1 * g) / G) + tid; p < (int)(((int64_t)P1 * (g + 1)) / G); p += FNT)
+                acc_clear[p] = 0;
+            if (g == 0) {
+                if (want_gn) {
+                    gn = warp_sum(gn);
+                    if ((tid & 31) == 0) s_red[tid >> 5] = gn;
                 }
-            }
-            if (epoch_end && g == 0 && tid == 0) {
-                const double L = 0.5 * sse_epoch * Cl;
-                if (a.loss_hist) a.loss_hist[e] = L;
-                if (!isfinite(L)) atomicOr(a.status, ST_NONFINITE);
-            }
-            const bool want_gn = a.gnorm_hist && epoch_end;
-            if (want_gn) {
-                __syncthreads();
-                if (lane == 0) s_red[warp] = gn;
                 __syncthreads();
                 if (tid == 0) {
-                    double t = 0.0;
-                    for (int q = 0; q < RE_NW; ++q) t += s_red[q];
-                    a.gnp[g] = t;
+                    sse_epoch += (double)__ldcg(acc + P) * (1.0 / 4294967296.0);
+                    if (epoch_end) {
+                        const double L = 0.5 * sse_epoch * Cl;
+                        if (a.loss_hist) a.loss_hist[e] = L;
+                        if (!isfinite(L)) atomicOr(a.status, ST_NONFINITE);
+                        if (want_gn) {
+                            double t = 0.0;
+                            for (int q = 0; q < RE_NW; ++q) t += s_red[q];
+                            a.gnorm_hist[e] = sqrt(t);
+                        }
+                    }
                 }
             }
-            if (!last_step) {
-                target += (unsigned long long)G;
-                if (!grid_barrier(a.bar, target, a.status)) return;
-                if (want_gn && g == 0 && warp == 0) {
-                    const double t = fixed_sum(a.gnp, G, lane);
-                    if (lane == 0) a.gnorm_hist[e] = sqrt(t);
-                }
-            } else if (want_gn) {
-                // The last block to finish folds the norm partials.
-                __syncthreads();
-                if (tid == 0) {
-                    __threadfence();
-                    s_last = (atomicAdd(a.bar + 1, 1ull) == a.ticket_base + (unsigned long long)G - 1);
-                    __threadfence();
-                }
-                __syncthreads();
-                if (s_last && warp == 0) {
-                    const double t = fixed_sum(a.gnp, G, lane);
-                    if (lane == 0) a.gnorm_hist[e] = sqrt(t);
-                }
-            }
+            __syncthreads();
         }
     }
+    if (g == 0)
+        for (int p = tid; p < P; p += FNT) a.params[p] = Wm[p];
 }
 
 template <int DP>
@@ -264,18 +231,28 @@ void *pick_kernel(int act, int H) {
 
 struct Choice {
     void *fn;
-    size_t smem;
+    int DP;
 };
 
 bool choose(int act, int D, int H, Choice *c) {
     if (D < 1 || H < 1 || H > 128) return false;
-    if (D <= 8) *c = {pick_kernel<8>(act, H), smem_bytes<8>(D, H)};
-    else if (D <= 16) *c = {pick_kernel<16>(act, H), smem_bytes<16>(D, H)};
-    else if (D <= 36) *c = {pick_kernel<36>(act, H), smem_bytes<36>(D, H)};
-    else if (D <= 48) *c = {pick_kernel<48>(act, H), smem_bytes<48>(D, H)};
-    else if (D <= 64) *c = {pick_kernel<64>(act, H), smem_bytes<64>(D, H)};
+    if (D <= 8) *c = {pick_kernel<8>(act, H), 8};
+    else if (D <= 16) *c = {pick_kernel<16>(act, H), 16};
+    else if (D <= 36) *c = {pick_kernel<36>(act, H), 36};
+    else if (D <= 48) *c = {pick_kernel<48>(act, H), 48};
+    else if (D <= 64) *c = {pick_kernel<64>(act, H), 64};
     else return false;
     return true;
+}
+
+size_t choice_smem(const Choice &c, int D, int H, int rows) {
+    switch (c.DP) {
+        case 8: return smem_bytes<8>(D, H, rows);
+        case 16: return smem_bytes<16>(D, H, rows);
+        case 36: return smem_bytes<36>(D, H, rows);
+        case 48: return smem_bytes<48>(D, H, rows);
+        default: return smem_bytes<64>(D, H, rows);
+    }
 }
 
 // Resident blocks per SM for (kernel, dynamic smem) on the current device,
@@ -326,16 +303,10 @@ size_t fused_scratch_bytes(int D, int H, int sms) {
 void fused_scratch_carve(void *base, int D, int H, int sms, FusedScratch *s) {
     (void)sms;
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    const size_t P = (size_t)(D + 2) * H + 1;
+    const size_t P1 = (size_t)(D + 2) * H + 2;
     char *b = (char *)base;
-    size_t off = 0;
-    s->part = (float *)(b + off);
-    off = al(off + sizeof(float) * GMAX * P);
-    s->lossp = (double *)(b + off);
-    off = al(off + sizeof(double) * GMAX);
-    s->gnp = (double *)(b + off);
-    off = al(off + sizeof(double) * GMAX);
-    s->bar = (unsigned long long *)(b + off);
+    s->acc = (long long *)b;
+    s->bar = (unsigned long long *)(b + al(sizeof(long long) * 3 * P1));
 }
 
 cudaError_t fused_train(int act, int D, int H, int64_t n, const float *X, const float *y, float *params,
@@ -344,20 +315,39 @@ cudaError_t fused_train(int act, int D, int H, int64_t n, const float *X, const 
                         int skip_block, cudaStream_t st, int *grid_used) {
     Choice ch;
     if (!choose(act, D, H, &ch)) return cudaErrorInvalidValue;
-    cudaError_t e;
-    int per_sm = blocks_per_sm(ch.fn, ch.smem, &e);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    const int sms = device_sm_count();
     const int64_t mbs = (mb <= 0 || mb >= n) ? n : mb;
     if (rows_per_block < 1) rows_per_block = 32;
     int64_t G = cdiv(mbs > 0 ? mbs : 1, rows_per_block);
-    if (G > (int64_t)per_sm * sms) G = (int64_t)per_sm * sms;
     if (G > GMAX) G = GMAX;
     if (G < 1) G = 1;
+    // Shared memory depends on whether the rows stay resident.
+    bool resident = (mbs == n) && cdiv(mbs, G) <= RESIDENT;
+    size_t smem = choice_smem(ch, D, H, resident ? RESIDENT : CAP);
+    cudaError_t e;
+    int per_sm = blocks_per_sm(ch.fn, smem, &e);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int64_t cap = (int64_t)per_sm * device_sm_count();
+    if (G > cap) {
+        G = cap;
+        resident = (mbs == n) && cdiv(mbs, G) <= RESIDENT;
+        smem = choice_smem(ch, D, H, resident ? RESIDENT : CAP);
+        per_sm = blocks_per_sm(ch.fn, smem, &e);
+        if (e != cudaSuccess) return e;
+        if ((int64_t)per_sm * device_sm_count() < G) return cudaErrorInvalidConfiguration;
+    }
     if (grid_used) *grid_used = (int)G;
     const int64_t steps = n > 0 ? cdiv(n, mbs) * (int64_t)epochs : 0;
     if (steps == 0) return cudaSuccess;
+    // Fixed-point scale of the gradient sums: 2^40 leaves 2^23 of range for a
+    // mean loss; a summed loss scales the range with the rows of a step.
+    int gshift = 40;
+    if (!loss_mean) {
+        int lg = 0;
+        while (((int64_t)1 << lg) < mbs) ++lg;
+        gshift = 40 - lg;
+        if (gshift < 8) gshift = 8;
+    }
     FArgs a;
     a.D = D;
     a.H = H;
@@ -369,23 +359,21 @@ cudaError_t fused_train(int act, int D, int H, int64_t n, const float *X, const 
     a.loss_mean = loss_mean;
     a.epochs = epochs;
     a.mb = mb;
+    a.gshift = gshift;
     a.loss_hist = loss_hist;
     a.gnorm_hist = gnorm_hist;
     a.status = status;
-    a.part = s.part;
-    a.lossp = s.lossp;
-    a.gnp = s.gnp;
+    a.acc = s.acc;
+    a.rot = ctr->rot;
     a.bar = s.bar;
     a.bar_base = ctr->bar;
-    a.ticket_base = ctr->ticket;
     a.skip_block = skip_block;
     void *args[] = {&a};
-    e = cudaLaunchCooperativeKernel(ch.fn, dim3((unsigned)G), dim3(FNT), args, ch.smem, st);
+    e = cudaLaunchCooperativeKernel(ch.fn, dim3((unsigned)G), dim3(FNT), args, smem, st);
     if (e != cudaSuccess) return e;
-    // Every block arrives at 2 * steps - 1 barriers and, when the norm is
-    // folded at the end, takes one ticket.
-    ctr->bar += (unsigned long long)G * (unsigned long long)(2 * steps - 1);
-    if (gnorm_hist) ctr->ticket += (unsigned long long)G;
+    // One barrier per step for every block; the accumulator rotates by a step.
+    ctr->bar += (unsigned long long)G * (unsigned long long)steps;
+    ctr->rot = (int)((ctr->rot + steps) % 3);
     return cudaSuccess;
 }
 

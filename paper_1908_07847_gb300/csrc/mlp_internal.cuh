@@ -204,16 +204,15 @@ cudaError_t plain_labels(int prec, int64_t n, const void *o, int8_t *labels, cud
 // ------------------------------------------------------- fused-path launcher
 
 struct FusedScratch {
-    float *part;              // G x P
-    double *lossp;            // G
-    double *gnp;              // G
-    unsigned long long *bar;  // [0] barrier arrivals, [1] finish tickets
+    long long *acc;           // 3 x (P + 1) fixed-point gradient accumulators
+    unsigned long long *bar;  // barrier arrival counter
 };
 
-// Host-side view of the counters: their values when the next launch starts.
+// Host-side view of the scratch state when the next launch starts: the
+// counter's value and which accumulator buffer is first (the other two are 0).
 struct FusedCounters {
     unsigned long long bar = 0;
-    unsigned long long ticket = 0;
+    int rot = 0;
 };
 
 // True if the fused cooperative kernel supports this shape.
