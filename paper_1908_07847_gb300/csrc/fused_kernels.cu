@@ -182,10 +182,22 @@ __global__ void __launch_bounds__(FNT, 2) k_fused_train(FArgs a) {
             // ---- every block applies the summed gradient to its own copy
             const bool want_gn = g == 0 && a.gnorm_hist && epoch_end;
             double gn = 0.0;
-            for (int p = tid; p < P; p += FNT) {
-                const float gsum = (float)__ldcg(acc + p) * gscale;
-                Wm[p] -= a.lr * gsum;
-                if (want_gn) gn = fma((double)gsum, (double)gsum, gn);
+            for (int base = 0; base < P; base += 8 * FNT) {
+                long long v[8];  // eight loads in flight per thread
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    const int p = base + r * FNT + tid;
+                    v[r] = (p < P) ? __ldcg(acc + p) : 0ll;
+                }
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    const int p = base + r * FNT + tid;
+                    if (p < P) {
+                        const float gsum = (float)v[r] * gscale;
+                        Wm[p] -= a.lr * gsum;
+                        if (want_gn) gn = fma((double)gsum, (double)gsum, gn);
+                    }
+                }
             }
             for (int p = (int)(((int64_t)P1 * g) / G) + tid; p < (int)(((int64_t)P1 * (g + 1)) / G); p += FNT)
                 acc_clear[p] = 0;
