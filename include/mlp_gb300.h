@@ -228,6 +228,35 @@ mlp_status mlp_batch_train(int32_t prec, int32_t act, int32_t D,
                            int32_t epochs, float lr, int32_t loss_mean,
                            void *stream);
 
+/*
+ * Fused training (as mlp_train_epochs, without the gradient norm) on
+ * caller-owned weights, allocating no device memory.  It is for callers that
+ * cannot call cudaMalloc: code that runs while a stream is being captured into
+ * a CUDA graph, a framework that hands out every byte of device memory from
+ * its own pool, or a real-time loop that must not block on the allocator.  The
+ * paper has no counterpart; it is a property of this library's interface.
+ *
+ * The kernel's scratch (fixed-point gradient accumulators, a barrier counter
+ * and a status word) lives in one statically sized device array of 203,520
+ * bytes that every GPU which loads this library holds until the process exits.
+ * Hence the limits D <= 64 and H <= 128; larger networks are rejected with
+ * MLP_EINVAL.  Every call uses that one array and clears it on `stream` before
+ * its kernel runs, so calls that overlap on the GPU (from two streams or two
+ * threads) race with each other and must be ordered by the caller.  The first
+ * call on a device also looks up the array's device address (and may load the
+ * library's device code); make that first call before any stream capture.
+ *
+ * X (n x D), y (n), params (packed [W1, b1, w2, b2], 16-byte aligned, trained
+ * in place) and loss_hist (epochs doubles, may be NULL) are device memory.
+ * status_out (device int32, may be NULL) receives 0, or the bit 1 if a
+ * cross-block wait gave up, or the bit 2 if the loss was not finite.
+ */
+mlp_status mlp_train_fused_noalloc(int32_t act, int32_t D, int32_t H, int64_t n,
+                                   const float *X, const float *y, float *params,
+                                   float lr, int32_t loss_mean, int32_t epochs,
+                                   int64_t minibatch, double *loss_hist,
+                                   int32_t *status_out, void *stream);
+
 /* Message of the last failure on the calling thread ("" if none). */
 const char *mlp_last_error(void);
 

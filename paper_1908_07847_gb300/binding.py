@@ -25,7 +25,7 @@ EXPORTS = [
     "mlp_forward", "mlp_backward", "mlp_update", "mlp_step_plain", "mlp_train_epochs",
     "mlp_train_host", "mlp_predict", "mlp_check", "mlp_workspace_bytes", "mlp_forward_w",
     "mlp_backward_w", "mlp_debug_skip_block", "mlp_set_rows_per_block", "mlp_batch_train",
-    "mlp_batch_create", "mlp_batch_run", "mlp_batch_check", "mlp_batch_destroy",
+    "mlp_batch_create", "mlp_batch_run", "mlp_batch_check", "mlp_batch_destroy", "mlp_train_fused_noalloc",
     "mlp_last_error", "mlp_version",
 ]
 
@@ -89,6 +89,7 @@ def lib():
             "mlp_batch_run": (S, [V, I32, V]),
             "mlp_batch_check": (S, [V, V]),
             "mlp_batch_destroy": (None, [V]),
+            "mlp_train_fused_noalloc": (S, [I32, I32, I32, I64, V, V, V, F, I32, I32, I64, V, V, V]),
             "mlp_last_error": (ctypes.c_char_p, []),
             "mlp_version": (ctypes.c_char_p, []),
         }
@@ -229,6 +230,14 @@ def mlp_batch_check(b, stream=0):
 
 def mlp_batch_destroy(b):
     lib().mlp_batch_destroy(b)
+
+
+def mlp_train_fused_noalloc(act, D, H, n, X, y, params, lr, loss_mean, epochs, minibatch=0, loss_hist=None,
+                            status_out=None, stream=0):
+    """Fused training that allocates no device memory (scratch in a fixed
+    device array; D <= 64, H <= 128; overlapping calls race)."""
+    return _ck(lib().mlp_train_fused_noalloc(act, D, H, n, _p(X), _p(y), _p(params), lr, loss_mean, epochs,
+                                             minibatch, _p(loss_hist), _p(status_out), stream))
 
 
 def mlp_last_error():

@@ -145,6 +145,9 @@ mlp_status check_handle(mlp_t h) {
 
 }  // namespace
 
+// Records the message of a failure in a translation unit of its own.
+mlp_status noalloc_fail(mlp_status s, const char *msg) { return fail(s, "%s", msg); }
+
 namespace mlp {
 int device_sm_count() {
     int dev = 0, n = 0;
