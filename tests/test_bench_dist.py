@@ -1,0 +1,47 @@
+"""The benchmark's multi-rank logic on CPU ranks (gloo, world size 2): the
+max-over-ranks time and the rank environment."""
+import os
+import socket
+
+import pytest
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _worker(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    r, w, l = bench.dist_env()
+    t = bench.aggregate_max(1.5 + rank, w)
+    bench.barrier(w)
+    q.put((r, w, l, t))
+    dist.destroy_process_group()
+
+
+def test_aggregate_max_over_two_gloo_ranks():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    ps = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in ps:
+        p.start()
+    out = sorted(q.get(timeout=120) for _ in ps)
+    for p in ps:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert out == [(0, 2, 0, 2.5), (1, 2, 1, 2.5)]
+
+
+def test_single_rank_identity():
+    import bench
+    assert bench.aggregate_max(3.25, 1) == 3.25
