@@ -39,7 +39,8 @@ WORKLOAD = "33-64-1 sigmoid MLP, full-batch GD lr 0.1, 4096 rows x 33 features, 
 METRIC = "train sample-steps/s (fwd+bwd+update) vs plain FP32 path on 1 GB300; % roofline"
 FLOPS_PER_SAMPLE = 4 * D_IN * H_HID + 10 * H_HID   # forward 2DH+3H, backward 2DH+7H
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
-FUSED_SRC = os.path.join(ROOT, "paper_1908_07847_gb300", "csrc", "fused_kernels.cu")
+FUSED_SRCS = [os.path.join(ROOT, "paper_1908_07847_gb300", "csrc", f)
+              for f in ("fused_kernels.cu", "row_engine.cuh", "mlp_internal.cuh")]
 
 
 def parse():
@@ -157,7 +158,10 @@ def traffic_from_profile():
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         rec = json.load(open(path))
-        src = hashlib.sha256(open(FUSED_SRC, "rb").read()).hexdigest()[:16]
+        h = hashlib.sha256()
+        for f in FUSED_SRCS:
+            h.update(open(f, "rb").read())
+        src = h.hexdigest()[:16]
         if rec.get("source_sha256_16") == src and rec.get("workload") == WORKLOAD:
             return rec.get("dram_bytes_per_launch")
     except Exception:

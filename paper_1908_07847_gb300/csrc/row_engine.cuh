@@ -86,13 +86,18 @@ struct RowEngine {
         // Squared errors of this call are summed in FP32 per lane and folded
         // into the FP64 sum once (FP64 arithmetic is slow on this part).
         float sse_f = 0.f;
-        for (int base = grp * RPI + slot * RB; base < cn + slot * RB; base += NG * RPI) {
-            int xo[RB];
+        // Row t of a slot's batch is base + t * nslots + slot: neighbouring
+        // segments read neighbouring rows, whose float4 words fall in distinct
+        // shared-memory banks (row stride DP = 4 mod 32 words or a multiple of 8).
+        const int nslots = 32 / S;
+        for (int base = grp * RPI; base < cn; base += NG * RPI) {
+            int xo[RB], rr[RB];
             bool valid[RB];
 #pragma unroll
             for (int t = 0; t < RB; ++t) {
-                valid[t] = base + t < cn;
-                xo[t] = (valid[t] ? base + t : 0) * DP;
+                rr[t] = base + t * nslots + slot;
+                valid[t] = rr[t] < cn;
+                xo[t] = (valid[t] ? rr[t] : 0) * DP;
             }
             float z[RB];
 #pragma unroll
@@ -145,7 +150,7 @@ struct RowEngine {
 #pragma unroll
             for (int t = 0; t < RB; ++t) {
                 const float o = sigmoid_out(zp[t] + b2);
-                const float err = o - ys[valid[t] ? base + t : 0];
+                const float err = o - ys[valid[t] ? rr[t] : 0];
                 const float d2 = valid[t] ? c * err * o * (1.0f - o) : 0.f;
                 if (valid[t]) sse_f = fmaf(err, err, sse_f);
                 gb2a += d2;
