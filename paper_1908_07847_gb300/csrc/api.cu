@@ -483,14 +483,89 @@ mlp_status mlp_backward_w(int32_t prec, int32_t act, int32_t D, int32_t H, int64
 
 struct mlp_batch {
     int device;
-    int act, D, Hmax, n_nets;
+    int prec, act, D, Hmax, n_nets;
     float lr;
     int loss_mean;
-    void *mem;                 // one allocation: nets, order, status
+    void *mem;                 // one allocation: nets (or tensor-core descriptors and maps), order, status
     mlp::BatchNet *nets;
+    void *tc_descs;
     int *order;
     int *status;
 };
+
+// BF16 plan: per-net TMA tensor maps and descriptors for the tcgen05 kernel.
+static mlp_status batch_create_tc(int32_t act, int32_t D, const mlp_net_desc *nets, int32_t n_nets, float lr,
+                                  int32_t loss_mean, mlp_batch_t *out) {
+    if (act != MLP_ACT_SIGMOID) return fail(MLP_EUNSUPPORTED, "mlp_batch_create: BF16 supports the sigmoid only");
+    std::vector<double> cost(n_nets);
+    for (int t = 0; t < n_nets; ++t) {
+        const mlp_net_desc &d = nets[t];
+        if (!mlp::tc_supported(D, d.H))
+            return fail(MLP_EINVAL, "mlp_batch_create: BF16 needs D %% 8 == 0, 8 <= D <= 56 and H in {128, 256} "
+                                    "(net %d: D=%d H=%d)", t, D, d.H);
+        if (d.n < 0 || !d.params || (d.n > 0 && (!d.X || !d.y)))
+            return fail(MLP_EINVAL, "mlp_batch_create: net %d has a null buffer or n < 0", t);
+        if (((uintptr_t)d.X & 15) != 0) return fail(MLP_EINVAL, "mlp_batch_create: net %d X not 16-byte aligned", t);
+        cost[t] = (double)d.n * d.H;
+    }
+    std::vector<int> order(n_nets);
+    for (int t = 0; t < n_nets; ++t) order[t] = t;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+    mlp_batch_t b = new (std::nothrow) mlp_batch();
+    if (!b) return fail(MLP_ENOMEM, "mlp_batch_create: host allocation");
+    if (cudaGetDevice(&b->device) != cudaSuccess) {
+        delete b;
+        return fail(MLP_ECUDA, "mlp_batch_create: no device");
+    }
+    b->prec = MLP_BF16;
+    b->act = act;
+    b->D = D;
+    b->Hmax = 256;
+    b->n_nets = n_nets;
+    b->lr = lr;
+    b->loss_mean = loss_mean ? 1 : 0;
+    b->nets = nullptr;
+    const size_t N1 = (size_t)(n_nets > 0 ? n_nets : 1);
+    const size_t mb = (mlp::tc_tmap_bytes() + 127) & ~(size_t)127;
+    const size_t db = (mlp::tc_desc_bytes() + 15) & ~(size_t)15;
+    const size_t maps = ((mb * N1) + 255) & ~(size_t)255;
+    const size_t descs = ((db * N1) + 255) & ~(size_t)255;
+    const size_t ords = ((sizeof(int) * N1) + 255) & ~(size_t)255;
+    if (cudaMalloc(&b->mem, maps + descs + ords + 256) != cudaSuccess) {
+        cudaGetLastError();
+        delete b;
+        return fail(MLP_ENOMEM, "mlp_batch_create: device allocation");
+    }
+    char *base = (char *)b->mem;
+    b->tc_descs = base + maps;
+    b->order = (int *)(base + maps + descs);
+    b->status = (int *)(base + maps + descs + ords);
+    std::vector<unsigned char> hmaps(mb * N1, 0), hdescs(db * N1, 0);
+    for (int t = 0; t < n_nets; ++t) {
+        const mlp_net_desc &d = nets[t];
+        cudaError_t e = mlp::tc_encode_map(hmaps.data() + mb * t, d.X, D, d.n);
+        if (e != cudaSuccess) {
+            cudaFree(b->mem);
+            delete b;
+            return fail(MLP_ECUDA, "mlp_batch_create: tensor map of net %d: %s", t, cudaGetErrorString(e));
+        }
+        mlp::tc_fill_desc(hdescs.data() + db * t, base + mb * t, d.y, d.params, d.loss_hist, d.n, d.H);
+    }
+    cudaError_t e = cudaSuccess;
+    if (n_nets > 0) {
+        e = cudaMemcpy(base, hmaps.data(), mb * n_nets, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(b->tc_descs, hdescs.data(), db * n_nets, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(b->order, order.data(), sizeof(int) * n_nets, cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) e = cudaMemset(b->status, 0, sizeof(int));
+    if (e != cudaSuccess) {
+        cudaFree(b->mem);
+        delete b;
+        return cuda_fail(e, "mlp_batch_create");
+    }
+    *out = b;
+    return MLP_OK;
+}
 
 extern "C" {
 
@@ -498,10 +573,11 @@ mlp_status mlp_batch_create(int32_t prec, int32_t act, int32_t D, const mlp_net_
                             float lr, int32_t loss_mean, mlp_batch_t *out) {
     if (!out) return fail(MLP_EINVAL, "mlp_batch_create: null out");
     *out = nullptr;
-    if (prec != MLP_FP32) return fail(MLP_EUNSUPPORTED, "mlp_batch_create: only MLP_FP32 in this build");
+    if (prec != MLP_FP32 && prec != MLP_BF16) return fail(MLP_EUNSUPPORTED, "mlp_batch_create: FP32 or BF16 only");
     if (act != MLP_ACT_SIGMOID && act != MLP_ACT_TANH) return fail(MLP_EINVAL, "mlp_batch_create: bad act");
-    if (D < 1 || D > mlp::batched_max_D()) return fail(MLP_EINVAL, "mlp_batch_create: D=%d out of 1..64", D);
     if (n_nets < 0 || (n_nets > 0 && !nets)) return fail(MLP_EINVAL, "mlp_batch_create: bad net list");
+    if (prec == MLP_BF16) return batch_create_tc(act, D, nets, n_nets, lr, loss_mean, out);
+    if (D < 1 || D > mlp::batched_max_D()) return fail(MLP_EINVAL, "mlp_batch_create: D=%d out of 1..64", D);
     int Hmax = 1;
     std::vector<mlp::BatchNet> host(n_nets);
     std::vector<double> cost(n_nets);
@@ -527,6 +603,8 @@ mlp_status mlp_batch_create(int32_t prec, int32_t act, int32_t D, const mlp_net_
         delete b;
         return fail(MLP_ECUDA, "mlp_batch_create: no device");
     }
+    b->prec = MLP_FP32;
+    b->tc_descs = nullptr;
     b->act = act;
     b->D = D;
     b->Hmax = Hmax;
@@ -562,6 +640,12 @@ mlp_status mlp_batch_run(mlp_batch_t b, int32_t epochs, void *stream) {
     if (!b) return fail(MLP_EINVAL, "mlp_batch_run: null plan");
     if (epochs < 0) return fail(MLP_EINVAL, "mlp_batch_run: epochs < 0");
     DeviceScope ds(b->device);
+    if (b->prec == MLP_BF16) {
+        CK(mlp::tc_batched_train(b->tc_descs, b->order, b->n_nets, b->D, epochs, b->lr, b->loss_mean, b->status,
+                                 (cudaStream_t)stream),
+           "tensor-core batched training kernel");
+        return MLP_OK;
+    }
     CK(mlp::batched_train(b->act, b->D, b->Hmax, b->nets, b->order, b->n_nets, epochs, b->lr, b->loss_mean,
                           b->status, (cudaStream_t)stream),
        "batched training kernel");
@@ -575,6 +659,7 @@ mlp_status mlp_batch_check(mlp_batch_t b, void *stream) {
     int st = 0;
     CK(cudaMemcpy(&st, b->status, sizeof(int), cudaMemcpyDeviceToHost), "mlp_batch_check read");
     CK(cudaMemset(b->status, 0, sizeof(int)), "mlp_batch_check clear");
+    if (st & mlp::ST_TIMEOUT) return fail(MLP_ETIMEOUT, "a wait inside the training kernel gave up");
     if (st & mlp::ST_NONFINITE) return fail(MLP_ENONFINITE, "a net's loss was not finite");
     return MLP_OK;
 }

@@ -248,6 +248,17 @@ void batched_smem_layout(int D, int Hmax, int *part_floats, int *wm_floats, size
 cudaError_t batched_train(int act, int D, int Hmax, const BatchNet *nets_dev, const int *order_dev, int n_nets,
                           int epochs, float lr, int loss_mean, int *status, cudaStream_t st);
 
+// ------------------------------------------- bf16 tensor-core (tcgen05) path
+
+bool tc_supported(int D, int H);
+size_t tc_desc_bytes();
+size_t tc_tmap_bytes();
+cudaError_t tc_encode_map(void *map, const void *X, int D, int64_t n);
+void tc_fill_desc(void *desc, const void *tmap_dev, const float *y, float *params, double *loss_hist, int64_t n,
+                  int H);
+cudaError_t tc_batched_train(const void *descs_dev, const int *order_dev, int n_nets, int D, int epochs, float lr,
+                             int loss_mean, int *status, cudaStream_t st);
+
 int device_sm_count();
 
 }  // namespace mlp

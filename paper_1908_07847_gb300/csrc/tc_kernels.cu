@@ -1,0 +1,572 @@
+// BF16 tensor-core (tcgen05) training of many independent D-H-1 networks, one
+// block per network for all epochs (Sec. 2.2 of arXiv 1908.07847: feed-forward,
+// output error, backpropagation, full-batch gradient descent, no momentum).
+//
+// Per tile of 128 rows of X (bf16, loaded by TMA into a 128-byte-swizzled tile):
+//   forward    Z1 = X W1^T           tcgen05.mma M = 128 rows, N = H, K = D,
+//                                    A = X tile (K-major), B = bf16 copy of W1
+//                                    (K-major), FP32 accumulator in tensor memory;
+//   epilogue   thread r of 4 warps owns row r (= tensor-memory lane r):
+//              h = sigmoid(z1 + b1), z2 = h w2 + b2, o = sigmoid(z2),
+//              d2 = c (o - y) o (1 - o), d1 = d2 w2 h (1 - h);
+//              h and d1 go to shared memory as bf16, transposed on the fly
+//              (MN-major operand tiles), d2 to a small K-major operand;
+//   gradient   gW1 += d1^T X         M = 128 hidden units, N = 64, K = 128 rows,
+//                                    A = d1 tile (MN-major), B = the same X tile
+//                                    read as MN-major; column D of the X tile is
+//                                    set to 1 so column D of the result is gb1;
+//              gw2 += h^T d2         M = 128, N = 16, K = 128 rows.
+// At the end of an epoch the epilogue threads read the accumulators (one hidden
+// unit per tensor-memory lane), update the FP32 master weights in global memory
+// (w -= lr g) and rebuild the bf16 copy of W1 for the next epoch.
+//
+// Roles: warp 0 issues the TMA loads, warp 1 issues the MMAs (one thread each),
+// warps 2..5 run the epilogue.  Every wait is bounded; on a timeout the block
+// records MLP_ETIMEOUT, stops issuing, drains what it issued (again bounded),
+// frees its tensor memory and leaves.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "mlp_internal.cuh"
+
+namespace mlp {
+
+namespace {
+
+constexpr int TR = 128;           // rows per tile
+constexpr int HMAX = 256;
+constexpr int NSTAGE = 2;
+constexpr int NT = 6 * 32;        // threads: TMA warp, MMA warp, 4 epilogue warps
+constexpr uint32_t TM_Z1 = 0;     // tensor-memory columns: Z1 [0, H)
+constexpr uint32_t TM_GW1 = 256;  // gW1 | gb1 for hidden block hb at 256 + 64 hb
+constexpr uint32_t TM_GW2 = 384;  // gw2 for hidden block hb at 384 + 16 hb
+
+// shared-memory layout (bytes); operand tiles 1024-byte aligned
+constexpr uint32_t SM_X = 0;                               // NSTAGE x 16 KB
+constexpr uint32_t SM_W1 = SM_X + NSTAGE * 16384;          // H x 128 B
+constexpr uint32_t SM_HT = SM_W1 + HMAX * 128;             // 4 x 16 KB (h^T)
+constexpr uint32_t SM_DT = SM_HT + 4 * 16384;              // 4 x 16 KB (d1^T)
+constexpr uint32_t SM_B3 = SM_DT + 4 * 16384;              // 4 KB (d2)
+constexpr uint32_t SM_B1 = SM_B3 + 4096;                   // fp32 b1
+constexpr uint32_t SM_W2 = SM_B1 + HMAX * 4;               // fp32 w2
+constexpr uint32_t SM_BAR = SM_W2 + HMAX * 4;              // mbarriers
+constexpr uint32_t SM_MISC = SM_BAR + 256;                 // tmem slot, flags, reductions
+constexpr uint32_t SM_TOTAL = SM_MISC + 256;
+constexpr uint32_t SM_ALLOC = SM_TOTAL + 1024;             // + alignment slack
+
+struct TcNet {
+    const CUtensorMap *tmap;  // X: bf16 [n x D], box 64 x 128, 128-byte swizzle
+    const float *y;           // n labels
+    float *params;            // packed FP32 [W1 (H x D), b1, w2, b2]
+    double *loss_hist;        // [epochs] or NULL
+    int64_t n;
+    int32_t H;
+    int32_t pad;
+};
+
+struct TcArgs {
+    const TcNet *nets;
+    const int *order;
+    int n_nets;
+    int D;
+    int epochs;
+    float lr;
+    int loss_mean;
+    int *status;
+};
+
+// ------------------------------------------------------------ PTX helpers
+
+__device__ __forceinline__ uint32_t s32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo, uint32_t swz) {
+    // tcgen05 shared-memory matrix descriptor: start, leading and stride byte
+    // offsets (>> 4), the fixed 0b001 at bits 46-48, swizzle mode at 61-63.
+    return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46) | ((uint64_t)(swz & 7) << 61);
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulator, bf16 A and B.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, int a_mn, int b_mn) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)a_mn << 15) | ((uint32_t)b_mn << 16) |
+           ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the phase of `parity` to complete.  Gives up (and raises
+// the block's abort flag) after WAIT_LIMIT_NS, or, unless `drain`, as soon as
+// another role has aborted.  Drain waits (for work already issued) ignore the
+// flag but keep the time limit.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort, bool drain = false) {
+    if (mbar_try(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try(bar, parity)) return true;
+        if ((it & 255) == 0) {
+            if (!drain && *abort) return false;
+            if (global_ns() - t0 > WAIT_LIMIT_NS) {
+                *abort = 1;
+                return false;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(dst), "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void proxy_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ float tmem_ld1(uint32_t taddr) {
+    uint32_t r;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    return __uint_as_float(r);
+}
+
+// sigmoid for the bf16 path: 1/2 + tanh(x/2)/2 from tanh.approx (relative error
+// about 2^-11, far below bf16's 2^-8).
+__device__ __forceinline__ float sigmoid_bf(float x) {
+    float t;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(0.5f * x));
+    return fmaf(0.5f, t, 0.5f);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t *>(&v);
+}
+__device__ __forceinline__ float bf_lo(uint32_t v) { return __uint_as_float(v << 16); }
+__device__ __forceinline__ float bf_hi(uint32_t v) { return __uint_as_float(v & 0xFFFF0000u); }
+
+// Byte offset of element (row, col) of a 128-byte-swizzled K-major tile whose
+// rows are 128 bytes (64 bf16), 8-row groups of 1024 bytes.
+__device__ __forceinline__ uint32_t kmajor_off(int row, int col) {
+    return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + ((((col >> 3) ^ (row & 7))) << 4) + (col & 7) * 2);
+}
+// Byte offset of the 16-byte chunk holding columns m..m+7 (m % 8 == 0) of row k
+// of an MN-major swizzled operand: atoms of 8 K-rows x 64 MN, 16 KB per MN atom
+// (16 K-groups of 1024 bytes).
+__device__ __forceinline__ uint32_t mnmajor_chunk(int m, int k) {
+    return (uint32_t)((m >> 6) * 16384 + (k >> 3) * 1024 + (k & 7) * 128 + ((((m & 63) >> 3) ^ (k & 7)) << 4));
+}
+
+__global__ void __launch_bounds__(NT, 1) k_tc_batched(TcArgs a) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *sm = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const uint32_t sb = s32(sm);
+    float *b1s = (float *)(sm + SM_B1);
+    float *w2s = (float *)(sm + SM_W2);
+    const uint32_t bar0 = sb + SM_BAR;
+    // mbarriers: full[2], empty[2], z1_full, z1_empty, a_full, a_empty, epoch_done, w_ready
+    const uint32_t BAR_FULL = bar0, BAR_EMPTY = bar0 + 16, BAR_Z1F = bar0 + 32, BAR_Z1E = bar0 + 40,
+                   BAR_AF = bar0 + 48, BAR_AE = bar0 + 56, BAR_EPOCH = bar0 + 64, BAR_W = bar0 + 72,
+                   BAR_DRAIN = bar0 + 80, BAR_EPI = bar0 + 88;
+    uint32_t *tmem_slot = (uint32_t *)(sm + SM_MISC);
+    volatile int *abort = (volatile int *)(sm + SM_MISC + 16);
+    float *red = (float *)(sm + SM_MISC + 64);     // 4 warps x (sse, gb2)
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int D = a.D;
+
+    if (tid == 0) {
+        for (int s = 0; s < NSTAGE; ++s) {
+            mbar_init(BAR_FULL + 8 * s, 1);
+            mbar_init(BAR_EMPTY + 8 * s, 1);
+        }
+        mbar_init(BAR_Z1F, 1);
+        mbar_init(BAR_Z1E, 128);
+        mbar_init(BAR_AF, 128);
+        mbar_init(BAR_AE, 1);
+        mbar_init(BAR_EPOCH, 1);
+        mbar_init(BAR_W, 128);
+        mbar_init(BAR_DRAIN, 1);
+        mbar_init(BAR_EPI, 128);
+        *abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(s32(tmem_slot)));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    // zero the d2 operand once (rows n = 1..15 stay zero)
+    for (int i = tid; i < 4096 / 4; i += NT) ((uint32_t *)(sm + SM_B3))[i] = 0u;
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    for (int idx = blockIdx.x; idx < a.n_nets; idx += gridDim.x) {
+        const TcNet nd = a.nets[a.order ? a.order[idx] : idx];
+        const int H = nd.H;
+        const int64_t n = nd.n;
+        const int T = (int)((n + TR - 1) / TR);
+        const int Dk = (D + 15) & ~15;        // forward K covered by MMAs
+        const float c = a.loss_mean ? 1.0f / (float)n : 1.0f;
+        const double Cl = a.loss_mean ? 1.0 / (double)n : 1.0;
+        float *P = nd.params;
+        const int HD = H * D;
+
+        // ---- weights into shared memory: bf16 W1 (swizzled, zero padded), b1, w2
+        for (int i = tid; i < H * 64; i += NT) {
+            const int j = i >> 6, k = i & 63;
+            const float v = (k < D) ? P[j * D + k] : 0.f;
+            *(__nv_bfloat16 *)(sm + SM_W1 + kmajor_off(j, k)) = __float2bfloat16_rn(v);
+        }
+        for (int j = tid; j < H; j += NT) {
+            b1s[j] = P[HD + j];
+            w2s[j] = P[HD + H + j];
+        }
+        proxy_fence();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        float b2 = P[HD + 2 * H];
+
+        if (T == 0 || a.epochs == 0) {
+            if (nd.loss_hist && tid == 0)
+                for (int e = 0; e < a.epochs; ++e) nd.loss_hist[e] = 0.0;
+            continue;
+        }
+
+        // Barrier phase counters restart for every net: the previous net's
+        // waits were all completed, so re-initialising is safe after a sync.
+        if (tid == 0) {
+            for (int s = 0; s < NSTAGE; ++s) {
+                asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(BAR_FULL + 8 * s));
+                asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(BAR_EMPTY + 8 * s));
+                mbar_init(BAR_FULL + 8 * s, 1);
+                mbar_init(BAR_EMPTY + 8 * s, 1);
+            }
+            const uint32_t others[8] = {BAR_Z1F, BAR_Z1E, BAR_AF, BAR_AE, BAR_EPOCH, BAR_W, BAR_DRAIN, BAR_EPI};
+            const uint32_t counts[8] = {1, 128, 128, 1, 1, 128, 1, 128};
+            for (int q = 0; q < 8; ++q) {
+                asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(others[q]));
+                mbar_init(others[q], counts[q]);
+            }
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        __syncthreads();
+
+        if (warp == 0) {
+            // ================= TMA producer =================
+            if (lane == 0) {
+                int it = 0;
+                for (int e = 0; e < a.epochs && !*abort; ++e)
+                    for (int t = 0; t < T; ++t, ++it) {
+                        const int s = it % NSTAGE, use = it / NSTAGE;
+                        if (!mbar_wait(BAR_EMPTY + 8 * s, (use & 1) ^ 1, abort)) break;
+                        mbar_expect_tx(BAR_FULL + 8 * s, 16384);
+                        tma_load_2d(sb + SM_X + 16384 * s, nd.tmap, 0, t * TR, BAR_FULL + 8 * s);
+                    }
+                // drain: every issued load completes before the block moves on
+                const int issued = it;
+                for (int q = (issued > NSTAGE ? issued - NSTAGE : 0); q < issued; ++q)
+                    mbar_wait(BAR_FULL + 8 * (q % NSTAGE), (q / NSTAGE) & 1, abort, true);
+            }
+        } else if (warp == 1) {
+            // ================= MMA issuer =================
+            if (lane == 0) {
+                const uint32_t id_fwd = idesc_bf16(128, H, 0, 0);
+                const uint32_t id_gw1 = idesc_bf16(128, 64, 1, 1);
+                const uint32_t id_gw2 = idesc_bf16(128, 16, 1, 0);
+                int it = 0, z1e_use = 0, af_use = 0;
+                auto grad = [&](int itp, int first) {
+                    const int s = itp % NSTAGE;
+                    const uint32_t xs = sb + SM_X + 16384 * s;
+                    for (int hb = 0; hb < H / 128; ++hb)
+                        for (int kk = 0; kk < TR / 16; ++kk) {
+                            const uint64_t ad = sdesc(sb + SM_DT + hb * 2 * 16384 + kk * 2048, 16384, 1024, 2);
+                            const uint64_t bd = sdesc(xs + kk * 2048, 16384, 1024, 2);
+                            mma_bf16(tmem + TM_GW1 + 64 * hb, ad, bd, id_gw1, (first && kk == 0) ? 0u : 1u);
+                            const uint64_t hd = sdesc(sb + SM_HT + hb * 2 * 16384 + kk * 2048, 16384, 1024, 2);
+                            const uint64_t d3 = sdesc(sb + SM_B3 + kk * 256, 128, 2048, 0);
+                            mma_bf16(tmem + TM_GW2 + 16 * hb, hd, d3, id_gw2, (first && kk == 0) ? 0u : 1u);
+                        }
+                    mma_commit(BAR_AE);
+                    mma_commit(BAR_EMPTY + 8 * s);
+                };
+                bool ok = true;
+                for (int e = 0; e < a.epochs && ok; ++e) {
+                    if (e > 0 && !mbar_wait(BAR_W, (e - 1) & 1, abort)) { ok = false; break; }
+                    tc_fence_after();
+                    for (int t = 0; t < T; ++t, ++it) {
+                        const int s = it % NSTAGE;
+                        if (!mbar_wait(BAR_FULL + 8 * s, (it / NSTAGE) & 1, abort)) { ok = false; break; }
+                        if (!mbar_wait(BAR_Z1E, (z1e_use++ & 1) ^ 1, abort)) { ok = false; break; }
+                        tc_fence_after();
+                        const uint32_t xs = sb + SM_X + 16384 * s;
+                        for (int ks = 0; ks < Dk / 16; ++ks)
+                            mma_bf16(tmem + TM_Z1, sdesc(xs + ks * 32, 16, 1024, 2),
+                                     sdesc(sb + SM_W1 + ks * 32, 16, 1024, 2), id_fwd, ks > 0 ? 1u : 0u);
+                        mma_commit(BAR_Z1F);
+                        if (t > 0) {
+                            if (!mbar_wait(BAR_AF, af_use++ & 1, abort)) { ok = false; break; }
+                            tc_fence_after();
+                            grad(it - 1, t == 1);
+                        }
+                    }
+                    if (!ok) break;
+                    if (!mbar_wait(BAR_AF, af_use++ & 1, abort)) { ok = false; break; }
+                    tc_fence_after();
+                    grad(it - 1, T == 1);
+                    mma_commit(BAR_EPOCH);
+                }
+                // drain every MMA issued before tensor memory is released
+                mma_commit(BAR_DRAIN);
+                mbar_wait(BAR_DRAIN, 0, abort, true);
+            }
+        } else {
+            // ================= epilogue: 4 warps, thread = row = TMEM lane =================
+            const int q = warp & 3;                 // tensor-memory lane quarter
+            const int r = q * 32 + lane;            // row within the tile / lane
+            const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
+            int z1f_use = 0, ae_use = 0, epi_use = 0;
+            bool ok = true;
+            // Barrier of the 128 epilogue threads with a bounded wait (an
+            // mbarrier, so that a block that aborts cannot leave it hanging).
+            auto epi_sync = [&]() -> bool {
+                mbar_arrive(BAR_EPI);
+                return mbar_wait(BAR_EPI, epi_use++ & 1, abort);
+            };
+            for (int e = 0; e < a.epochs && ok; ++e) {
+                float sse = 0.f, gb2s = 0.f;
+                for (int t = 0; t < T; ++t) {
+                    const int64_t row = (int64_t)t * TR + r;
+                    const bool valid = row < n;
+                    const float yv = valid ? nd.y[row] : 0.f;
+                    if (!mbar_wait(BAR_Z1F, z1f_use++ & 1, abort)) { ok = false; break; }
+                    // the previous tile's gradient MMAs must be done with h^T, d1^T, d2
+                    if (!mbar_wait(BAR_AE, (ae_use++ & 1) ^ 1, abort)) { ok = false; break; }
+                    tc_fence_after();
+                    // pass 1: h = sigmoid(z1 + b1) -> h^T (bf16), z2 partial
+                    float zp = 0.f;
+                    for (int c0 = 0; c0 < H; c0 += 32) {
+                        float z[32];
+                        tmem_ld32(lane_base + TM_Z1 + c0, z);
+                        uint32_t pk[16];
+#pragma unroll
+                        for (int i = 0; i < 32; i += 2) {
+                            const float h0 = sigmoid_bf(z[i] + b1s[c0 + i]);
+                            const float h1 = sigmoid_bf(z[i + 1] + b1s[c0 + i + 1]);
+                            zp = fmaf(h0, w2s[c0 + i], zp);
+                            zp = fmaf(h1, w2s[c0 + i + 1], zp);
+                            pk[i >> 1] = pack_bf16(h0, h1);
+                        }
+#pragma unroll
+                        for (int v = 0; v < 4; ++v)
+                            *(uint4 *)(sm + SM_HT + mnmajor_chunk(c0 + 8 * v, r)) =
+                                make_uint4(pk[4 * v], pk[4 * v + 1], pk[4 * v + 2], pk[4 * v + 3]);
+                    }
+                    tc_fence_before();
+                    mbar_arrive(BAR_Z1E);  // Z1 in tensor memory may be overwritten
+                    const float o = sigmoid_bf(zp + b2);
+                    const float err = o - yv;
+                    const float d2 = valid ? c * err * o * (1.0f - o) : 0.f;
+                    if (valid) sse = fmaf(err, err, sse);
+                    gb2s += d2;
+                    // d2 operand (n = 0, k = r) and the ones column of the X tile
+                    *(__nv_bfloat16 *)(sm + SM_B3 + (r & 7) * 2 + (r >> 3) * 128) = __float2bfloat16_rn(d2);
+                    const int s = (e * T + t) % NSTAGE;
+                    *(__nv_bfloat16 *)(sm + SM_X + 16384 * s + kmajor_off(r, D)) = __float2bfloat16_rn(1.0f);
+                    // pass 2: d1 = d2 w2 h (1 - h) -> d1^T (bf16)
+                    for (int c0 = 0; c0 < H; c0 += 8) {
+                        const uint4 hv = *(const uint4 *)(sm + SM_HT + mnmajor_chunk(c0, r));
+                        const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w};
+                        uint32_t dk[4];
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) {
+                            const float h0 = bf_lo(hw[v]), h1 = bf_hi(hw[v]);
+                            const float d10 = d2 * w2s[c0 + 2 * v] * (h0 - h0 * h0);
+                            const float d11 = d2 * w2s[c0 + 2 * v + 1] * (h1 - h1 * h1);
+                            dk[v] = pack_bf16(d10, d11);
+                        }
+                        *(uint4 *)(sm + SM_DT + mnmajor_chunk(c0, r)) = make_uint4(dk[0], dk[1], dk[2], dk[3]);
+                    }
+                    proxy_fence();
+                    mbar_arrive(BAR_AF);
+                }
+                if (!ok) break;
+                // ---- end of epoch: reductions and the update
+                if (!mbar_wait(BAR_EPOCH, e & 1, abort)) { ok = false; break; }
+                tc_fence_after();
+                float ws = warp_sum(sse), wg = warp_sum(gb2s);
+                // fixed order over the 4 epilogue warps (by lane quarter)
+                if (lane == 0) {
+                    red[2 * q] = ws;
+                    red[2 * q + 1] = wg;
+                }
+                if (!epi_sync()) { ok = false; break; }
+                double sse_t = 0.0;
+                float gb2 = 0.f;
+                for (int w = 0; w < 4; ++w) {
+                    sse_t += (double)red[2 * w];
+                    gb2 += red[2 * w + 1];
+                }
+                for (int hb = 0; hb < H / 128; ++hb) {
+                    const int j = hb * 128 + r;  // hidden unit = lane
+                    float g[64];
+                    tmem_ld32(lane_base + TM_GW1 + 64 * hb, *reinterpret_cast<float(*)[32]>(&g[0]));
+                    tmem_ld32(lane_base + TM_GW1 + 64 * hb + 32, *reinterpret_cast<float(*)[32]>(&g[32]));
+                    const float gw2 = tmem_ld1(lane_base + TM_GW2 + 16 * hb);
+                    for (int k = 0; k < D; ++k) {
+                        const float w = P[j * D + k] - a.lr * g[k];
+                        P[j * D + k] = w;
+                        *(__nv_bfloat16 *)(sm + SM_W1 + kmajor_off(j, k)) = __float2bfloat16_rn(w);
+                    }
+                    const float nb1 = b1s[j] - a.lr * g[D];
+                    const float nw2 = w2s[j] - a.lr * gw2;
+                    P[HD + j] = nb1;
+                    P[HD + H + j] = nw2;
+                    b1s[j] = nb1;
+                    w2s[j] = nw2;
+                }
+                b2 -= a.lr * gb2;
+                if (r == 0) {
+                    P[HD + 2 * H] = b2;
+                    const double L = 0.5 * Cl * sse_t;
+                    if (nd.loss_hist) nd.loss_hist[e] = L;
+                    if (!isfinite(L)) atomicOr(a.status, ST_NONFINITE);
+                }
+                proxy_fence();
+                tc_fence_before();
+                if (!epi_sync()) { ok = false; break; }
+                mbar_arrive(BAR_W);
+            }
+        }
+        if (*abort && tid == 0) atomicOr(a.status, ST_TIMEOUT);
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (*abort) break;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static std::mutex mu;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+}  // namespace
+
+size_t tc_desc_bytes() { return sizeof(TcNet); }
+size_t tc_tmap_bytes() { return sizeof(CUtensorMap); }
+
+bool tc_supported(int D, int H) { return D >= 8 && D <= 56 && D % 8 == 0 && (H == 128 || H == 256); }
+
+// Encodes the tensor map of one net's X (bf16 n x D, row-major) into *map.
+cudaError_t tc_encode_map(void *map, const void *X, int D, int64_t n) {
+    PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+    if (!fn) return cudaErrorNotSupported;
+    if (((uintptr_t)X & 15) != 0) return cudaErrorInvalidValue;
+    cuuint64_t dims[2] = {(cuuint64_t)D, (cuuint64_t)(n > 0 ? n : 1)};
+    cuuint64_t strides[1] = {(cuuint64_t)D * 2};
+    cuuint32_t box[2] = {64, TR};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn((CUtensorMap *)map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(X), dims, strides,
+                    box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// Fills the device-side descriptor (host image) of one net.
+void tc_fill_desc(void *desc, const void *tmap_dev, const float *y, float *params, double *loss_hist, int64_t n,
+                  int H) {
+    TcNet *d = (TcNet *)desc;
+    d->tmap = (const CUtensorMap *)tmap_dev;
+    d->y = y;
+    d->params = params;
+    d->loss_hist = loss_hist;
+    d->n = n;
+    d->H = H;
+    d->pad = 0;
+}
+
+cudaError_t tc_batched_train(const void *descs_dev, const int *order_dev, int n_nets, int D, int epochs, float lr,
+                             int loss_mean, int *status, cudaStream_t st) {
+    if (n_nets == 0 || epochs == 0) return cudaSuccess;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_tc_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM_ALLOC);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    TcArgs a;
+    a.nets = (const TcNet *)descs_dev;
+    a.order = order_dev;
+    a.n_nets = n_nets;
+    a.D = D;
+    a.epochs = epochs;
+    a.lr = lr;
+    a.loss_mean = loss_mean;
+    a.status = status;
+    const int grid = n_nets < device_sm_count() ? n_nets : device_sm_count();
+    k_tc_batched<<<grid, NT, SM_ALLOC, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace mlp

@@ -1,0 +1,101 @@
+"""BF16 tensor-core (tcgen05) path of the many-nets plan against the FP64 oracle
+(Sec. 2.2 of arXiv 1908.07847), on the same bf16-exact inputs.  Tolerance: the
+gradient within 2e-2 (max-norm relative), as stated for bf16 arithmetic."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import Params
+from paper_1908_07847_gb300 import binding as B
+from paper_1908_07847_gb300 import inputs as I
+from tests.gpu_util import BF16_GRAD_TOL, dev, host, lr32, rel_err_elem, rel_err_norm, stream
+
+pytestmark = pytest.mark.gpu
+
+D_REAL, D_PAD = 33, 48
+
+
+def make_net(seed, n, H):
+    X = I.bf16_round(I.features(seed, n, D_REAL, D_PAD))
+    T = Params(*I.teacher_weights(D=D_REAL, Dpad=D_PAD))
+    y = oracle.predict(X, T).astype(np.float32)
+    W = I.init_weights(seed + 7, D_REAL, H, D_PAD)
+    return X, y, W
+
+
+def run_tc(nets, epochs, lr):
+    import torch
+    keep, descs, params, losses = [], [], [], []
+    for X, y, W in nets:
+        Xd = dev(I.bf16_bits(X).view(np.int16))
+        yd = dev(y)
+        P = dev(np.concatenate([W[0].ravel(), W[1], W[2], W[3]]).astype(np.float32))
+        L = torch.zeros(max(epochs, 1), dtype=torch.float64, device="cuda")
+        keep += [Xd, yd]
+        params.append(P)
+        losses.append(L)
+        descs.append(B.mlp_net_desc(W[0].shape[0], X.shape[0], Xd.data_ptr(), yd.data_ptr(), P.data_ptr(),
+                                    L.data_ptr()))
+    b = B.mlp_batch_create(B.MLP_BF16, B.MLP_ACT_SIGMOID, D_PAD, descs, lr, 1)
+    try:
+        B.mlp_batch_run(b, epochs, stream())
+        st = B.mlp_batch_check(b, stream())
+    finally:
+        B.mlp_batch_destroy(b)
+    assert st == B.MLP_OK, B.mlp_last_error()
+    return [host(p).astype(np.float64) for p in params], [host(l)[:epochs] for l in losses]
+
+
+def flat(W):
+    return np.concatenate([np.asarray(W[0]).ravel(), W[1], W[2], np.asarray(W[3]).ravel()]).astype(np.float64)
+
+
+SHAPES = [(1, 128), (100, 128), (128, 256), (129, 256), (300, 128), (1000, 256)]
+
+
+def test_one_epoch_gradient_matches_oracle():
+    """With lr = 1 one epoch moves the weights by exactly -g (FP32 master)."""
+    nets = [make_net(500 + i, n, H) for i, (n, H) in enumerate(SHAPES)]
+    got, _ = run_tc(nets, 1, 1.0)
+    for (X, y, W), P, (n, H) in zip(nets, got, SHAPES):
+        g = flat(W) - P
+        ref = oracle.mse_gradients(X, y, Params(*W))
+        exp = np.concatenate([ref[0].ravel(), ref[1], ref[2], [ref[3]]])
+        assert rel_err_norm(g, exp) <= BF16_GRAD_TOL, (n, H)
+        HD = H * D_PAD
+        assert rel_err_norm(g[HD:HD + H], ref[1]) <= BF16_GRAD_TOL, ("gb1", n, H)
+        assert rel_err_norm(g[HD + H:HD + 2 * H], ref[2]) <= BF16_GRAD_TOL, ("gw2", n, H)
+        assert abs(g[-1] - ref[3]) <= BF16_GRAD_TOL * max(abs(ref[3]), np.max(np.abs(exp))), ("gb2", n, H)
+        # padded input columns never move
+        assert np.all(P[:HD].reshape(H, D_PAD)[:, D_REAL:] == 0.0)
+
+
+def test_training_tracks_oracle_and_accuracy():
+    """30 epochs at lr 0.1: loss history within 2e-2 of the oracle's and the
+    train accuracy within one point."""
+    shapes = [(2000, 128), (3000, 256)]
+    nets = [make_net(900 + i, n, H) for i, (n, H) in enumerate(shapes)]
+    epochs = 30
+    got, gl = run_tc(nets, epochs, lr32())
+    for (X, y, W), P, L, (n, H) in zip(nets, got, gl, shapes):
+        q, lh, _ = oracle.train(X, y, Params(*W), lr32(), epochs)
+        assert rel_err_elem(L, lh) <= 2e-2, (n, H)
+        HD = H * D_PAD
+        pg = Params(P[:HD].reshape(H, D_PAD), P[HD:HD + H], P[HD + H:HD + 2 * H], P[-1])
+        acc_gpu = (oracle.predict(X, pg) == y).mean()
+        acc_ref = (oracle.predict(X, q) == y).mean()
+        assert abs(acc_gpu - acc_ref) <= 0.01, (acc_gpu, acc_ref)
+
+
+def test_tc_batch_is_deterministic_and_validates():
+    nets = [make_net(1300 + i, n, H) for i, (n, H) in enumerate([(257, 128), (640, 256)])]
+    a, la = run_tc(nets, 3, lr32())
+    b, lb = run_tc(nets, 3, lr32())
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+    import torch
+    P = torch.zeros(1024, device="cuda")
+    bad = B.mlp_net_desc(100, 5, P.data_ptr(), P.data_ptr(), P.data_ptr(), 0)
+    with pytest.raises(B.MLPError) as e:
+        B.mlp_batch_create(B.MLP_BF16, 0, D_PAD, [bad], 0.1, 1)
+    assert e.value.status == B.MLP_EINVAL
