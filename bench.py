@@ -49,9 +49,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c1", choices=["c1", "c2"],
+    ap.add_argument("--workload", default="c1", choices=["c1", "c2", "c4"],
                     help="c1: the 33-64-1 full-batch workload (default line); "
-                         "c2: 4096 independent 33-H-1 nets, 500 epochs per step")
+                         "c2: 4096 independent 33-H-1 nets, 500 epochs per step; "
+                         "c4: 1024 independent 48-256-1 nets on bf16 tensor cores, 200 epochs per step")
     return ap.parse_args()
 
 
@@ -426,6 +427,93 @@ def run_c2(args, rank, world, local):
         print(json.dumps(out), flush=True)
 
 
+# ----------------------------------------- bf16 tensor-core workload (c4) --
+
+C4_NETS, C4_EPOCHS, C4_H, C4_D = 1024, 200, 256, 48
+C4_WORKLOAD = ("1024 independent 48-256-1 sigmoid MLPs (33 features zero-padded to 48), n ~ U{4096..16384}, "
+               "bf16 X on tcgen05 tensor cores, FP32 master weights, full-batch GD lr 0.1, 200 epochs per step")
+
+
+def run_c4(args, rank, world, local):
+    import torch
+    from paper_1908_07847_gb300 import binding as B
+    from paper_1908_07847_gb300 import inputs as I
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream().cuda_stream
+    seed = 4 + rank
+    _, ns = I.batched_shapes(seed, C4_NETS, (C4_H, C4_H), (4096, 16384))
+    offs = np.concatenate([[0], np.cumsum(ns)])
+    total = int(offs[-1])
+    Xall = torch.zeros((total, C4_D), dtype=torch.bfloat16, device=dev)
+    chunk = 1 << 20
+    for r0 in range(0, total, chunk):
+        r1 = min(total, r0 + chunk)
+        Xc = I.features(I.subseed(seed, 10_000 + r0 // chunk), r1 - r0, 33, C4_D)
+        Xall[r0:r1] = torch.from_numpy(Xc).to(dev).to(torch.bfloat16)
+    T = I.teacher_weights(D=33, Dpad=C4_D)
+    th = B.mlp_create(C4_D, T[0].shape[0], LR, 1, B.MLP_BF16, B.MLP_ACT_SIGMOID)
+    B.mlp_set_weights(th, *T)
+    lab = torch.zeros(total, dtype=torch.int8, device=dev)
+    B.mlp_predict(th, Xall, total, lab, stream)
+    B.mlp_destroy(th)
+    yall = lab.to(torch.float32)
+    P_per = (C4_D + 2) * C4_H + 1
+    P0 = torch.from_numpy(np.concatenate([np.concatenate([a.ravel() for a in I.init_weights(
+        I.subseed(seed, 200 + t), 33, C4_H, C4_D)]) for t in range(C4_NETS)])).to(dev)
+    Pw = P0.clone()
+    descs = [B.mlp_net_desc(C4_H, int(ns[t]), Xall[int(offs[t]):].data_ptr(), yall[int(offs[t]):].data_ptr(),
+                            Pw[t * P_per:].data_ptr(), None) for t in range(C4_NETS)]
+    plan = B.mlp_batch_create(B.MLP_BF16, B.MLP_ACT_SIGMOID, C4_D, descs, LR, 1)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    g = torch.cuda.CUDAGraph()
+    s2 = torch.cuda.Stream()
+    s2.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s2):
+        B.mlp_batch_run(plan, C4_EPOCHS, s2.cuda_stream)   # warm-up outside capture
+        s2.synchronize()
+        with torch.cuda.graph(g, stream=s2):
+            B.mlp_batch_run(plan, C4_EPOCHS, s2.cuda_stream)
+    torch.cuda.current_stream().wait_stream(s2)
+    for _ in range(max(args.warmup, 1)):
+        Pw.copy_(P0)
+        g.replay()
+    torch.cuda.synchronize()
+    times = []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            Pw.copy_(P0)
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            g.replay()
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1) * 1e-3)
+    assert B.mlp_batch_check(plan, stream) == B.MLP_OK, B.mlp_last_error()
+    B.mlp_batch_destroy(plan)
+    T_f = aggregate_max(sum(times), world)
+    units = int(ns.sum()) * C4_EPOCHS * world
+    # algorithmic tensor-core work per row-epoch: X W1^T and d1^T X (2 D H each),
+    # gb1 and gw2 (2 H each)
+    mma_flops = float(ns.sum()) * C4_EPOCHS * (4 * C4_D * C4_H + 4 * C4_H)
+    launch_s = statistics.mean(times)
+    peak = 1731.1   # MEASURED_PEAKS.json bf16_tflops_sustained
+    out = {
+        "metric": METRIC, "value": units * args.steps / T_f, "unit": "sample-steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": T_f / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": C4_WORKLOAD, "nets": C4_NETS, "rows_total": int(ns.sum()), "epochs_per_step": C4_EPOCHS,
+                   "l2": "inputs (1 GB of bf16 X) larger than L2; L2 also flushed between timed steps"},
+        "roofline": {"bound": "tensor", "achieved": mma_flops / launch_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+                     "frac": mma_flops / launch_s / 1e12 / peak, "traffic": None, "kernel": "k_tc_batched",
+                     "peak_basis": "bf16_tflops_sustained of measured", "flops_per_launch": mma_flops},
+        "gpu_launches": args.steps, "clocks": clk.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -438,6 +526,8 @@ def main():
         run_reference(args, rank, world)
     elif args.workload == "c2":
         run_c2(args, rank, world, local)
+    elif args.workload == "c4":
+        run_c4(args, rank, world, local)
     else:
         run_ours(args, rank, world, local)
     if world > 1 and args.impl == "ours":

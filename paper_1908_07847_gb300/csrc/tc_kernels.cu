@@ -21,7 +21,9 @@
 // (w -= lr g) and rebuild the bf16 copy of W1 for the next epoch.
 //
 // Roles: warp 0 issues the TMA loads, warp 1 issues the MMAs (one thread each),
-// warps 2..5 run the epilogue.  Every wait is bounded; on a timeout the block
+// warps 2..9 run the epilogue: the two warps that share a tensor-memory lane
+// quarter take one half of the hidden columns each and add their halves of z2
+// through shared memory.  Every wait is bounded; on a timeout the block
 // records MLP_ETIMEOUT, stops issuing, drains what it issued (again bounded),
 // frees its tensor memory and leaves.
 #include <cuda.h>
@@ -39,7 +41,9 @@ namespace {
 constexpr int TR = 128;           // rows per tile
 constexpr int HMAX = 256;
 constexpr int NSTAGE = 2;
-constexpr int NT = 6 * 32;        // threads: TMA warp, MMA warp, 4 epilogue warps
+constexpr int NEPI = 8;           // epilogue warps: two per tensor-memory lane quarter
+constexpr int NT = (2 + NEPI) * 32;  // threads: TMA warp, MMA warp, epilogue warps
+constexpr uint32_t NEPI_T = NEPI * 32;
 constexpr uint32_t TM_Z1 = 0;     // tensor-memory columns: Z1 [0, H)
 constexpr uint32_t TM_GW1 = 256;  // gW1 | gb1 for hidden block hb at 256 + 64 hb
 constexpr uint32_t TM_GW2 = 384;  // gw2 for hidden block hb at 384 + 16 hb
@@ -54,7 +58,8 @@ constexpr uint32_t SM_B1 = SM_B3 + 4096;                   // fp32 b1
 constexpr uint32_t SM_W2 = SM_B1 + HMAX * 4;               // fp32 w2
 constexpr uint32_t SM_BAR = SM_W2 + HMAX * 4;              // mbarriers
 constexpr uint32_t SM_MISC = SM_BAR + 256;                 // tmem slot, flags, reductions
-constexpr uint32_t SM_TOTAL = SM_MISC + 256;
+constexpr uint32_t SM_ZX = SM_MISC + 256;                  // z2 halves: 2 parities x 2 halves x 128 rows
+constexpr uint32_t SM_TOTAL = SM_ZX + 2 * 2 * 128 * 4;
 constexpr uint32_t SM_ALLOC = SM_TOTAL + 1024;             // + alignment slack
 
 struct TcNet {
@@ -225,13 +230,13 @@ __global__ void __launch_bounds__(NT, 1) k_tc_batched(TcArgs a) {
             mbar_init(BAR_EMPTY + 8 * s, 1);
         }
         mbar_init(BAR_Z1F, 1);
-        mbar_init(BAR_Z1E, 128);
-        mbar_init(BAR_AF, 128);
+        mbar_init(BAR_Z1E, NEPI_T);
+        mbar_init(BAR_AF, NEPI_T);
         mbar_init(BAR_AE, 1);
         mbar_init(BAR_EPOCH, 1);
-        mbar_init(BAR_W, 128);
+        mbar_init(BAR_W, NEPI_T);
         mbar_init(BAR_DRAIN, 1);
-        mbar_init(BAR_EPI, 128);
+        mbar_init(BAR_EPI, NEPI_T);
         *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -289,7 +294,7 @@ __global__ void __launch_bounds__(NT, 1) k_tc_batched(TcArgs a) {
                 mbar_init(BAR_EMPTY + 8 * s, 1);
             }
             const uint32_t others[8] = {BAR_Z1F, BAR_Z1E, BAR_AF, BAR_AE, BAR_EPOCH, BAR_W, BAR_DRAIN, BAR_EPI};
-            const uint32_t counts[8] = {1, 128, 128, 1, 1, 128, 1, 128};
+            const uint32_t counts[8] = {1, NEPI_T, NEPI_T, 1, 1, NEPI_T, 1, NEPI_T};
             for (int q = 0; q < 8; ++q) {
                 asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(others[q]));
                 mbar_init(others[q], counts[q]);
@@ -367,21 +372,25 @@ __global__ void __launch_bounds__(NT, 1) k_tc_batched(TcArgs a) {
                 mbar_wait(BAR_DRAIN, 0, abort, true);
             }
         } else {
-            // ================= epilogue: 4 warps, thread = row = TMEM lane =================
+            // ========== epilogue: thread = row = TMEM lane, one half of the columns ==========
             const int q = warp & 3;                 // tensor-memory lane quarter
+            const int half = (warp - 2) >> 2;      // which half of the hidden columns
             const int r = q * 32 + lane;            // row within the tile / lane
             const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
+            const int cw = H / 2, cb = half * cw;   // this thread's columns [cb, cb + cw)
+            float *zx = (float *)(sm + SM_ZX);
             int z1f_use = 0, ae_use = 0, epi_use = 0;
             bool ok = true;
-            // Barrier of the 128 epilogue threads with a bounded wait (an
-            // mbarrier, so that a block that aborts cannot leave it hanging).
+            // Barrier of the epilogue threads with a bounded wait (an mbarrier,
+            // so that a block that aborts cannot leave it hanging).
             auto epi_sync = [&]() -> bool {
                 mbar_arrive(BAR_EPI);
                 return mbar_wait(BAR_EPI, epi_use++ & 1, abort);
             };
+            int tcount = 0;
             for (int e = 0; e < a.epochs && ok; ++e) {
                 float sse = 0.f, gb2s = 0.f;
-                for (int t = 0; t < T; ++t) {
+                for (int t = 0; t < T; ++t, ++tcount) {
                     const int64_t row = (int64_t)t * TR + r;
                     const bool valid = row < n;
                     const float yv = valid ? nd.y[row] : 0.f;
@@ -389,9 +398,9 @@ __global__ void __launch_bounds__(NT, 1) k_tc_batched(TcArgs a) {
                     // the previous tile's gradient MMAs must be done with h^T, d1^T, d2
                     if (!mbar_wait(BAR_AE, (ae_use++ & 1) ^ 1, abort)) { ok = false; break; }
                     tc_fence_after();
-                    // pass 1: h = sigmoid(z1 + b1) -> h^T (bf16), z2 partial
+                    // pass 1: h = sigmoid(z1 + b1) -> h^T (bf16), half of z2
                     float zp = 0.f;
-                    for (int c0 = 0; c0 < H; c0 += 32) {
+                    for (int c0 = cb; c0 < cb + cw; c0 += 32) {
                         float z[32];
                         tmem_ld32(lane_base + TM_Z1 + c0, z);
                         uint32_t pk[16];
@@ -410,17 +419,22 @@ __global__ void __launch_bounds__(NT, 1) k_tc_batched(TcArgs a) {
                     }
                     tc_fence_before();
                     mbar_arrive(BAR_Z1E);  // Z1 in tensor memory may be overwritten
-                    const float o = sigmoid_bf(zp + b2);
+                    float *zxp = zx + (tcount & 1) * 256;
+                    zxp[half * 128 + r] = zp;
+                    if (!epi_sync()) { ok = false; break; }
+                    const float o = sigmoid_bf(zxp[r] + zxp[128 + r] + b2);
                     const float err = o - yv;
                     const float d2 = valid ? c * err * o * (1.0f - o) : 0.f;
-                    if (valid) sse = fmaf(err, err, sse);
-                    gb2s += d2;
-                    // d2 operand (n = 0, k = r) and the ones column of the X tile
-                    *(__nv_bfloat16 *)(sm + SM_B3 + (r & 7) * 2 + (r >> 3) * 128) = __float2bfloat16_rn(d2);
-                    const int s = (e * T + t) % NSTAGE;
-                    *(__nv_bfloat16 *)(sm + SM_X + 16384 * s + kmajor_off(r, D)) = __float2bfloat16_rn(1.0f);
+                    if (half == 0) {
+                        if (valid) sse = fmaf(err, err, sse);
+                        gb2s += d2;
+                        // d2 operand (n = 0, k = r) and the ones column of the X tile
+                        *(__nv_bfloat16 *)(sm + SM_B3 + (r & 7) * 2 + (r >> 3) * 128) = __float2bfloat16_rn(d2);
+                        const int s = tcount % NSTAGE;
+                        *(__nv_bfloat16 *)(sm + SM_X + 16384 * s + kmajor_off(r, D)) = __float2bfloat16_rn(1.0f);
+                    }
                     // pass 2: d1 = d2 w2 h (1 - h) -> d1^T (bf16)
-                    for (int c0 = 0; c0 < H; c0 += 8) {
+                    for (int c0 = cb; c0 < cb + cw; c0 += 8) {
                         const uint4 hv = *(const uint4 *)(sm + SM_HT + mnmajor_chunk(c0, r));
                         const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w};
                         uint32_t dk[4];
@@ -440,9 +454,9 @@ __global__ void __launch_bounds__(NT, 1) k_tc_batched(TcArgs a) {
                 // ---- end of epoch: reductions and the update
                 if (!mbar_wait(BAR_EPOCH, e & 1, abort)) { ok = false; break; }
                 tc_fence_after();
-                float ws = warp_sum(sse), wg = warp_sum(gb2s);
-                // fixed order over the 4 epilogue warps (by lane quarter)
-                if (lane == 0) {
+                const float ws = warp_sum(sse), wg = warp_sum(gb2s);
+                // fixed order over the four half-0 warps (by lane quarter)
+                if (half == 0 && lane == 0) {
                     red[2 * q] = ws;
                     red[2 * q + 1] = wg;
                 }
@@ -453,7 +467,9 @@ __global__ void __launch_bounds__(NT, 1) k_tc_batched(TcArgs a) {
                     sse_t += (double)red[2 * w];
                     gb2 += red[2 * w + 1];
                 }
-                for (int hb = 0; hb < H / 128; ++hb) {
+                // hidden unit of this thread: block hb = half (H = 256) or 0 (H = 128)
+                if (half < H / 128) {
+                    const int hb = half;
                     const int j = hb * 128 + r;  // hidden unit = lane
                     float g[64];
                     tmem_ld32(lane_base + TM_GW1 + 64 * hb, *reinterpret_cast<float(*)[32]>(&g[0]));
@@ -472,7 +488,7 @@ __global__ void __launch_bounds__(NT, 1) k_tc_batched(TcArgs a) {
                     w2s[j] = nw2;
                 }
                 b2 -= a.lr * gb2;
-                if (r == 0) {
+                if (half == 0 && r == 0) {
                     P[HD + 2 * H] = b2;
                     const double L = 0.5 * Cl * sse_t;
                     if (nd.loss_hist) nd.loss_hist[e] = L;
