@@ -159,6 +159,19 @@ __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence:
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void proxy_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
+// Wait for the tensor-memory loads of this thread; the registers are tied to
+// the wait so that the compiler cannot move their uses above it.
+__device__ __forceinline__ void tmem_wait_regs(uint32_t (&r)[32]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
+                   "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
+                   "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+                 :
+                 : "memory");
+}
+
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     uint32_t r[32];
     asm volatile(
@@ -169,14 +182,26 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
           "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
           "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    tmem_wait_regs(r);
 #pragma unroll
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
+// Issue a 32-column tensor-memory load without waiting (pair with tmem_wait).
+__device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+}
+
 __device__ __forceinline__ float tmem_ld1(uint32_t taddr) {
     uint32_t r;
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(r) : : "memory");
     return __uint_as_float(r);
 }
 
@@ -390,37 +415,47 @@ __global__ void __launch_bounds__(NT, 1) k_tc_batched(TcArgs a) {
             int tcount = 0;
             for (int e = 0; e < a.epochs && ok; ++e) {
                 float sse = 0.f, gb2s = 0.f;
+                float y_next = (r < n) ? nd.y[r] : 0.f;  // label of this thread's row, one tile ahead
                 for (int t = 0; t < T; ++t, ++tcount) {
                     const int64_t row = (int64_t)t * TR + r;
                     const bool valid = row < n;
-                    const float yv = valid ? nd.y[row] : 0.f;
+                    const float yv = y_next;
+                    if (row + TR < n) y_next = nd.y[row + TR];
                     if (!mbar_wait(BAR_Z1F, z1f_use++ & 1, abort)) { ok = false; break; }
                     // the previous tile's gradient MMAs must be done with h^T, d1^T, d2
                     if (!mbar_wait(BAR_AE, (ae_use++ & 1) ^ 1, abort)) { ok = false; break; }
                     tc_fence_after();
-                    // pass 1: h = sigmoid(z1 + b1) -> h^T (bf16), half of z2
-                    float zp = 0.f;
+                    // pass 1: h = sigmoid(z1 + b1) -> h^T (bf16), half of z2; the
+                    // next 32 columns are loaded from tensor memory while these are
+                    // processed, and z2 is summed in four independent chains
+                    float zp[4] = {0.f, 0.f, 0.f, 0.f};
+                    uint32_t zr[32];
+                    tmem_ld32_async(lane_base + TM_Z1 + cb, zr);
+                    tmem_wait_regs(zr);
                     for (int c0 = cb; c0 < cb + cw; c0 += 32) {
                         float z[32];
-                        tmem_ld32(lane_base + TM_Z1 + c0, z);
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) z[i] = __uint_as_float(zr[i]);
+                        if (c0 + 32 < cb + cw) tmem_ld32_async(lane_base + TM_Z1 + c0 + 32, zr);
                         uint32_t pk[16];
 #pragma unroll
                         for (int i = 0; i < 32; i += 2) {
                             const float h0 = sigmoid_bf(z[i] + b1s[c0 + i]);
                             const float h1 = sigmoid_bf(z[i + 1] + b1s[c0 + i + 1]);
-                            zp = fmaf(h0, w2s[c0 + i], zp);
-                            zp = fmaf(h1, w2s[c0 + i + 1], zp);
+                            zp[(i >> 1) & 3] = fmaf(h0, w2s[c0 + i], zp[(i >> 1) & 3]);
+                            zp[(i >> 1) & 3] = fmaf(h1, w2s[c0 + i + 1], zp[(i >> 1) & 3]);
                             pk[i >> 1] = pack_bf16(h0, h1);
                         }
 #pragma unroll
                         for (int v = 0; v < 4; ++v)
                             *(uint4 *)(sm + SM_HT + mnmajor_chunk(c0 + 8 * v, r)) =
                                 make_uint4(pk[4 * v], pk[4 * v + 1], pk[4 * v + 2], pk[4 * v + 3]);
+                        tmem_wait_regs(zr);
                     }
                     tc_fence_before();
                     mbar_arrive(BAR_Z1E);  // Z1 in tensor memory may be overwritten
                     float *zxp = zx + (tcount & 1) * 256;
-                    zxp[half * 128 + r] = zp;
+                    zxp[half * 128 + r] = (zp[0] + zp[1]) + (zp[2] + zp[3]);
                     if (!epi_sync()) { ok = false; break; }
                     const float o = sigmoid_bf(zxp[r] + zxp[128 + r] + b2);
                     const float err = o - yv;
