@@ -35,6 +35,7 @@ struct mlp_net {
     size_t lstage_cap = 0;
     int skip_block = -1;
     int rows_per_block = 32;
+    int max_clusters = 1 << 30;   // cap on clusters of the tensor-core kernel
     mlp::FusedCounters ctr;   // fused-kernel counter values at the next launch
 };
 
@@ -326,6 +327,19 @@ mlp_status mlp_train_epochs(mlp_t h, const void *X, const void *y, int64_t n, in
                             h->cfg.lr, h->cfg.loss_mean, epochs, minibatch, loss_hist, gnorm_hist, h->status,
                             fsc, &h->ctr, h->rows_per_block, h->skip_block, st, nullptr),
            "fused training kernel");
+        return MLP_OK;
+    }
+    if (h->cfg.prec == MLP_BF16 && h->cfg.act == MLP_ACT_SIGMOID && !gnorm_hist && mlp::tc_cluster_supported(D, H)) {
+        void *before = h->fs;
+        mlp_status s = grow(&h->fs, &h->fs_cap, mlp::tc_cluster_scratch_bytes(D, H), "cluster scratch");
+        if (s) return s;
+        if (h->fs != before) {
+            CK(cudaMemsetAsync(h->fs, 0, h->fs_cap, st), "cluster scratch reset");
+            h->ctr = mlp::FusedCounters();
+        }
+        CK(mlp::tc_cluster_train(X, (const float *)y, (float *)h->params, D, H, n, epochs, minibatch, h->cfg.lr,
+                                 h->cfg.loss_mean, loss_hist, h->status, h->fs, h->max_clusters, &h->ctr, st),
+           "tensor-core cluster kernel");
         return MLP_OK;
     }
     // Plain path, one step at a time.

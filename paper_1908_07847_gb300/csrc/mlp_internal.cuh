@@ -259,6 +259,16 @@ void tc_fill_desc(void *desc, const void *tmap_dev, const float *y, float *param
 cudaError_t tc_batched_train(const void *descs_dev, const int *order_dev, int n_nets, int D, int epochs, float lr,
                              int loss_mean, int *status, cudaStream_t st);
 
+// One wide network (H = 256..2048, a multiple of 256) trained by clusters of
+// H/256 blocks; scratch of tc_cluster_scratch_bytes(), all zero before the first
+// launch (the counters in *ctr then zero too).
+bool tc_cluster_supported(int D, int H);
+size_t tc_cluster_scratch_bytes(int D, int H);
+int tc_cluster_max_clusters(int H);
+cudaError_t tc_cluster_train(const void *X, const float *y, float *params, int D, int H, int64_t n, int epochs,
+                             int64_t mb, float lr, int loss_mean, double *loss_hist, int *status, void *scratch,
+                             int max_clusters, FusedCounters *ctr, cudaStream_t st);
+
 int device_sm_count();
 
 }  // namespace mlp

@@ -1,0 +1,141 @@
+"""BF16 tensor-core (tcgen05) training of one wide network (clusters of H/256
+blocks sharing z2 through distributed shared memory; Sec. 2.2 of arXiv
+1908.07847: forward, output error, backpropagation, w <- w - lr g) against the
+FP64 oracle on the same bf16-exact inputs.  Bars: the gradient within 2e-2
+(max-norm relative), train and test accuracy within one point."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import Params
+from paper_1908_07847_gb300 import binding as B
+from paper_1908_07847_gb300 import inputs as I
+from tests.gpu_util import BF16_GRAD_TOL, Net, dev, host, labels_from_teacher, lr32, rel_err_elem, rel_err_norm, \
+    stream
+
+pytestmark = pytest.mark.gpu
+
+D_REAL, D_PAD = 33, 48
+
+
+def make(seed, n, H):
+    X = I.bf16_round(I.features(seed, n, D_REAL, D_PAD))
+    y = labels_from_teacher(X, D_REAL)
+    W = I.init_weights(seed + 1, D_REAL, H, D_PAD)
+    return X, y, W
+
+
+def flat(W):
+    return np.concatenate([np.asarray(W[0]).ravel(), W[1], W[2], np.asarray(W[3]).ravel()]).astype(np.float64)
+
+
+def unflat(p, H):
+    HD = H * D_PAD
+    return Params(p[:HD].reshape(H, D_PAD), p[HD:HD + H], p[HD + H:HD + 2 * H], p[-1])
+
+
+def run(X, y, W, epochs, lr, mb=0, loss_mean=1):
+    import torch
+    H = W[0].shape[0]
+    with Net(D_PAD, H, lr, loss_mean, B.MLP_BF16) as net:
+        net.set(W)
+        Xd = dev(I.bf16_bits(X).view(np.int16))
+        yd = dev(y)
+        L = torch.zeros(max(epochs, 1), dtype=torch.float64, device="cuda")
+        B.mlp_train_epochs(net.h, Xd, yd, X.shape[0], epochs, mb, L, None, stream())
+        st = net.check()
+        assert st == B.MLP_OK, B.mlp_last_error()
+        return net.flat(), host(L)[:epochs]
+
+
+ONE_STEP = [(1, 256), (100, 256), (128, 512), (777, 768), (1000, 1024), (2500, 2048)]
+
+
+@pytest.mark.parametrize("n,H", ONE_STEP)
+def test_one_step_gradient_matches_oracle(n, H):
+    """Full batch, lr = 1: one epoch moves the FP32 master weights by -g."""
+    X, y, W = make(3000 + n + H, n, H)
+    got, _ = run(X, y, W, 1, 1.0)
+    g = flat(W) - got
+    ref = oracle.mse_gradients(X, y, Params(*W))
+    exp = np.concatenate([ref[0].ravel(), ref[1], ref[2], [ref[3]]])
+    assert rel_err_norm(g, exp) <= BF16_GRAD_TOL
+    HD = H * D_PAD
+    assert rel_err_norm(g[HD:HD + H], ref[1]) <= BF16_GRAD_TOL, "gb1"
+    assert rel_err_norm(g[HD + H:HD + 2 * H], ref[2]) <= BF16_GRAD_TOL, "gw2"
+    assert abs(g[-1] - ref[3]) <= BF16_GRAD_TOL * max(abs(ref[3]), np.max(np.abs(exp))), "gb2"
+    # padded input columns carry zero gradient
+    assert np.all(got[:HD].reshape(H, D_PAD)[:, D_REAL:] == 0.0)
+
+
+def test_sum_loss_gradient():
+    """c = 1 (loss_mean = 0): the gradient is the plain sum over rows."""
+    n, H = 3000, 512
+    X, y, W = make(3100, n, H)
+    lr = 1e-3
+    got, _ = run(X, y, W, 1, lr, loss_mean=0)
+    g = (flat(W) - got) / lr
+    ref = oracle.mse_gradients(X, y, Params(*W), loss_mean=False)
+    exp = np.concatenate([ref[0].ravel(), ref[1], ref[2], [ref[3]]])
+    assert rel_err_norm(g, exp) <= BF16_GRAD_TOL
+
+
+def test_minibatch_training_tracks_oracle():
+    """Contiguous mini-batches with a ragged last one: loss history, weight
+    change and accuracy against the oracle's run of the same schedule."""
+    n, H, mb, epochs = 5000, 512, 2048, 4
+    X, y, W = make(3200, n, H)
+    got, L = run(X, y, W, epochs, lr32(), mb=mb)
+    q, lh, _ = oracle.train(X, y, Params(*W), lr32(), epochs, minibatch=mb)
+    assert rel_err_elem(L, lh) <= BF16_GRAD_TOL
+    d_gpu, d_ref = got - flat(W), q.flat() - flat(W)
+    assert rel_err_norm(d_gpu, d_ref) <= 2 * BF16_GRAD_TOL
+    acc_gpu = (oracle.predict(X, unflat(got, H)) == y).mean()
+    acc_ref = (oracle.predict(X, q) == y).mean()
+    assert abs(acc_gpu - acc_ref) <= 0.01
+
+
+def test_wide_net_train_and_test_accuracy():
+    """48-2048-1, 75 / 25 split, mini-batch 1024: final train and test accuracy
+    within one point of the oracle's."""
+    n, H, mb, epochs = 8192, 2048, 1024, 3
+    X, y, W = make(3300, n, H)
+    ntr = I.split_count(n)
+    got, L = run(X[:ntr], y[:ntr], W, epochs, lr32(), mb=mb)
+    q, lh, _ = oracle.train(X[:ntr], y[:ntr], Params(*W), lr32(), epochs, minibatch=mb)
+    assert rel_err_elem(L, lh) <= BF16_GRAD_TOL
+    pg = unflat(got, H)
+    for rows in (slice(0, ntr), slice(ntr, n)):
+        a_gpu = (oracle.predict(X[rows], pg) == y[rows]).mean()
+        a_ref = (oracle.predict(X[rows], q) == y[rows]).mean()
+        assert abs(a_gpu - a_ref) <= 0.01, (rows, a_gpu, a_ref)
+
+
+def test_deterministic_and_continues_across_calls():
+    """Fixed-point cross-cluster sums: two runs agree bit for bit; two calls of
+    one epoch each equal one call of two epochs."""
+    n, H, mb = 2000, 768, 512
+    X, y, W = make(3400, n, H)
+    a, la = run(X, y, W, 2, lr32(), mb=mb)
+    b, lb = run(X, y, W, 2, lr32(), mb=mb)
+    assert np.array_equal(a, b) and np.array_equal(la, lb)
+    import torch
+    with Net(D_PAD, H, lr32(), 1, B.MLP_BF16) as net:
+        net.set(W)
+        Xd = dev(I.bf16_bits(X).view(np.int16))
+        yd = dev(y)
+        for _ in range(2):
+            B.mlp_train_epochs(net.h, Xd, yd, n, 1, mb, None, None, stream())
+        assert net.check() == B.MLP_OK
+        assert np.array_equal(net.flat(), a)
+
+
+def test_nonfinite_loss_is_reported():
+    n, H = 300, 256
+    X, y, W = make(3500, n, H)
+    y = y.copy()
+    y[7] = np.inf
+    with Net(D_PAD, H, lr32(), 1, B.MLP_BF16) as net:
+        net.set(W)
+        B.mlp_train_epochs(net.h, dev(I.bf16_bits(X).view(np.int16)), dev(y), n, 2, 0, None, None, stream())
+        assert net.check() == B.MLP_ENONFINITE
