@@ -49,9 +49,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c1", choices=["c1", "c2", "c4"],
+    ap.add_argument("--workload", default="c1", choices=["c1", "c2", "c3", "c4"],
                     help="c1: the 33-64-1 full-batch workload (default line); "
                          "c2: 4096 independent 33-H-1 nets, 500 epochs per step; "
+                         "c3: one 48-2048-1 net on bf16 tensor cores, 1M rows, mini-batch 8192, one epoch per step; "
                          "c4: 1024 independent 48-256-1 nets on bf16 tensor cores, 200 epochs per step")
     return ap.parse_args()
 
@@ -431,6 +432,142 @@ def run_c2(args, rank, world, local):
         print(json.dumps(out), flush=True)
 
 
+# --------------------------------- one wide bf16 tensor-core net (c3) ------
+
+C3_N, C3_D, C3_H, C3_MB, C3_SUB = 1 << 20, 48, 2048, 8192, 8192
+C3_WORKLOAD = ("one 48-2048-1 sigmoid MLP (33 features zero-padded to 48), 1,048,576 rows, bf16 X on tcgen05 "
+               "tensor cores (clusters of 8 blocks), FP32 master weights, mini-batch 8192, lr 0.1, one epoch per step")
+
+
+def c3_inputs(dev, seed=1908):
+    """1M seeded rows in bf16 on the device (33 N(0,1) features, zero padding),
+    teacher-net labels by the library's predict; returns X, y and init weights."""
+    import torch
+    from paper_1908_07847_gb300 import binding as B
+    from paper_1908_07847_gb300 import inputs as I
+    X = torch.zeros((C3_N, C3_D), dtype=torch.bfloat16, device=dev)
+    chunk = 1 << 18
+    for r0 in range(0, C3_N, chunk):
+        Xc = I.features(I.subseed(seed, 20_000 + r0 // chunk), chunk, 33, C3_D)
+        X[r0:r0 + chunk] = torch.from_numpy(Xc).to(dev).to(torch.bfloat16)
+    T = I.teacher_weights(D=33, Dpad=C3_D)
+    th = B.mlp_create(C3_D, T[0].shape[0], LR, 1, B.MLP_BF16, B.MLP_ACT_SIGMOID)
+    B.mlp_set_weights(th, *T)
+    lab = torch.zeros(C3_N, dtype=torch.int8, device=dev)
+    B.mlp_predict(th, X, C3_N, lab, torch.cuda.current_stream().cuda_stream)
+    B.mlp_destroy(th)
+    W = [np.ascontiguousarray(np.asarray(a, np.float32)) for a in I.init_weights(I.INIT_SEED + 3, 33, C3_H, C3_D)]
+    return X, lab.to(torch.float32), W
+
+
+def c3_oracle_leg(X, W):
+    """The FP64 oracle on one mini-batch step over the first 8192 rows (labels by
+    the oracle's teacher predict), timed; the library's step on the same rows,
+    compared.  Returns (cpu_baseline dict, parity dict)."""
+    import torch
+    import oracle
+    from paper_1908_07847_gb300 import binding as B
+    from paper_1908_07847_gb300 import inputs as I
+    Xs = X[:C3_SUB].float().cpu().numpy().astype(np.float64)
+    ys = oracle.predict(Xs, oracle.Params(*I.teacher_weights(D=33, Dpad=C3_D))).astype(np.float64)
+    p0 = oracle.Params(*[a.astype(np.float64) for a in W])
+    t0 = time.perf_counter()
+    q, _, _ = oracle.train(Xs, ys, p0, float(np.float32(LR)), 1, minibatch=C3_MB)
+    dt = time.perf_counter() - t0
+    h = B.mlp_create(C3_D, C3_H, LR, 1, B.MLP_BF16, B.MLP_ACT_SIGMOID)
+    try:
+        B.mlp_set_weights(h, *W)
+        yd = torch.from_numpy(ys.astype(np.float32)).to(X.device)
+        B.mlp_train_epochs(h, X[:C3_SUB].contiguous(), yd, C3_SUB, 1, C3_MB, None, None,
+                           torch.cuda.current_stream().cuda_stream)
+        assert B.mlp_check(h, torch.cuda.current_stream().cuda_stream) == B.MLP_OK, B.mlp_last_error()
+        W1 = np.zeros((C3_H, C3_D), np.float32)
+        b1, w2, b2 = np.zeros(C3_H, np.float32), np.zeros(C3_H, np.float32), np.zeros(1, np.float32)
+        B.mlp_get_weights(h, W1, b1, w2, b2)
+    finally:
+        B.mlp_destroy(h)
+    flat = lambda a, b, c, d: np.concatenate([np.ravel(a), np.ravel(b), np.ravel(c), np.ravel(d)]).astype(np.float64)
+    w0 = flat(*W)
+    dg, dr = flat(W1, b1, w2, b2) - w0, q.flat() - w0
+    err = float(np.max(np.abs(dg - dr)) / np.max(np.abs(dr)))
+    cpu = {"value": C3_SUB / dt, "unit": "sample-steps/s", "cores": 1, "kind": "oracle",
+           "sample": "one mini-batch step over the first %d rows (serial FP64 C oracle, one thread)" % C3_SUB}
+    parity = {"rows": C3_SUB, "steps": 1, "measure": "max |dw - dw*| / max |dw*| of the weight update",
+              "value": err, "tolerance": 2e-2}
+    return cpu, parity
+
+
+def run_c3(args, rank, world, local):
+    import torch
+    from paper_1908_07847_gb300 import binding as B
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream().cuda_stream
+    X, y, W = c3_inputs(dev, 1908 + rank)
+    h = B.mlp_create(C3_D, C3_H, LR, 1, B.MLP_BF16, B.MLP_ACT_SIGMOID)
+    B.mlp_set_weights(h, *W)
+    loss = torch.zeros(1, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        B.mlp_train_epochs(h, X, y, C3_N, 1, C3_MB, loss, None, stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier(world)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        for s0, e0 in ev:
+            flush.zero_()
+            s0.record()
+            step()
+            e0.record()
+        torch.cuda.synchronize()
+    times = [s0.elapsed_time(e0) * 1e-3 for s0, e0 in ev]
+    assert B.mlp_check(h, stream) == B.MLP_OK, B.mlp_last_error()
+    # e2e: host X, y through mlp_train_host (staged to the device every step)
+    Xh = X.cpu().pin_memory()
+    yh = y.cpu().pin_memory()
+    lh = torch.zeros(1, dtype=torch.float64).pin_memory()
+    e2e_steps = max(3, args.steps // 4)
+    B.mlp_train_host(h, Xh, yh, C3_N, 1, C3_MB, lh, stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        B.mlp_train_host(h, Xh, yh, C3_N, 1, C3_MB, lh, stream)
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    B.mlp_destroy(h)
+    barrier(world)
+    T_f = aggregate_max(sum(times), world)
+    T_e = aggregate_max(t_e2e, world)
+    units = C3_N * world
+    launch_s = statistics.mean(times)
+    # algorithmic tensor-core work per row: X W1^T, d1^T [X | 1] (2 D H + 2 H
+    # each) and h^T d2 (2 H)
+    mma_flops = float(C3_N) * (4 * C3_D * C3_H + 6 * C3_H)
+    peak = 1731.1   # MEASURED_PEAKS.json bf16_tflops_sustained
+    out = {
+        "metric": METRIC, "value": units * args.steps / T_f, "unit": "sample-steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": T_f / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": C3_WORKLOAD, "n": C3_N, "D": C3_D, "H": C3_H, "minibatch": C3_MB,
+                   "updates_per_step": C3_N // C3_MB,
+                   "l2": "flushed between timed steps (256 MiB write, outside the timed intervals)"},
+        "e2e": {"value": units * e2e_steps / T_e, "unit": "sample-steps/s",
+                "h2d_bytes_per_step": C3_N * C3_D * 2 + C3_N * 4, "d2h_bytes_per_step": 8,
+                "call": "mlp_train_host (pinned host X, y in; loss out)"},
+        "roofline": {"bound": "tensor", "achieved": mma_flops / launch_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+                     "frac": mma_flops / launch_s / 1e12 / peak, "traffic": None, "kernel": "k_tc_cluster",
+                     "peak_basis": "bf16_tflops_sustained of measured", "flops_per_launch": mma_flops},
+        "gpu_launches": args.steps, "clocks": clk.summary(),
+    }
+    if rank == 0:
+        out["cpu_baseline"], out["parity"] = c3_oracle_leg(X, W)
+        print(json.dumps(out), flush=True)
+
+
 # ----------------------------------------- bf16 tensor-core workload (c4) --
 
 C4_NETS, C4_EPOCHS, C4_H, C4_D = 1024, 200, 256, 48
@@ -530,6 +667,8 @@ def main():
         run_reference(args, rank, world)
     elif args.workload == "c2":
         run_c2(args, rank, world, local)
+    elif args.workload == "c3":
+        run_c3(args, rank, world, local)
     elif args.workload == "c4":
         run_c4(args, rank, world, local)
     else:
