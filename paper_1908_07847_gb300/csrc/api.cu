@@ -424,6 +424,7 @@ mlp_status mlp_check(mlp_t h, void *stream) {
         }
         return fail(MLP_ETIMEOUT, "a cross-block wait gave up");
     }
+    if (st & mlp::ST_BADLAUNCH) return fail(MLP_ECUDA, "a kernel was launched without its cluster shape");
     if (st & mlp::ST_NONFINITE) return fail(MLP_ENONFINITE, "a loss was not finite");
     return MLP_OK;
 }

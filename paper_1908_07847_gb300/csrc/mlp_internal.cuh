@@ -14,6 +14,7 @@ namespace mlp {
 // Device status bits (mlp_net::status).
 constexpr int ST_TIMEOUT = 1;
 constexpr int ST_NONFINITE = 2;
+constexpr int ST_BADLAUNCH = 4;   // a kernel found its launch shape wrong and did nothing
 
 // A cross-block wait gives up after this many nanoseconds.
 constexpr unsigned long long WAIT_LIMIT_NS = 1000000000ull;

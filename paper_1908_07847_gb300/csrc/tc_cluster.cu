@@ -97,6 +97,16 @@ __device__ __forceinline__ void cluster_sync_all() {
 }
 
 __global__ void __launch_bounds__(NT, 1) k_tc_cluster(const __grid_constant__ CUtensorMap tmap, ClArgs a) {
+    // Launch-shape check before any tensor-memory, cluster or peer access: the
+    // kernel needs clusters of exactly H/256 blocks of NT threads.
+    {
+        uint32_t ncta;
+        asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(ncta));
+        if ((int)ncta * HS != a.H || gridDim.x % ncta != 0 || blockDim.x != NT || a.H > 8 * HS) {
+            if (threadIdx.x == 0) atomicOr(a.status, ST_BADLAUNCH);
+            return;
+        }
+    }
     extern __shared__ unsigned char smem_raw[];
     unsigned char *sm = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const uint32_t sb = s32(sm);
@@ -288,30 +298,38 @@ __global__ void __launch_bounds__(NT, 1) k_tc_cluster(const __grid_constant__ CU
                     if (!mbar_wait(BAR_Z1F, z1f_use++ & 1, abort)) { eok = false; break; }
                     if (!mbar_wait(BAR_HE, (he_use++ & 1) ^ 1, abort)) { eok = false; break; }
                     tc_fence_after();
-                    // pass 1: h = sigmoid(z1) in bf16 pairs (kept for pass 2 and
-                    // written as h^T), this block's share of z2 = h w2 in FP32
+                    // pass 1: h = sigmoid(z1) in bf16 pairs (written as h^T), this
+                    // block's share of z2 = h w2 in FP32; two 32-column loads in flight
                     uint32_t hp[64];
                     float zp[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-                    for (int ch = 0; ch < 4; ++ch) {
-                        const int c0 = cb + 32 * ch;
-                        float z[32];
-                        tmem_ld32(lane_base + TM_Z1 + c0, z);
+                    for (int cp = 0; cp < 2; ++cp) {
+                        uint32_t zr2[2][32];
+                        tmem_ld32_async(lane_base + TM_Z1 + cb + 64 * cp, zr2[0]);
+                        tmem_ld32_async(lane_base + TM_Z1 + cb + 64 * cp + 32, zr2[1]);
+                        tmem_wait_regs(zr2[0]);
+                        tmem_tie_regs(zr2[1]);
 #pragma unroll
-                        for (int u = 0; u < 16; ++u) hp[16 * ch + u] = sigmoid_half_bf2(pack_bf16(z[2 * u], z[2 * u + 1]));
+                        for (int hh = 0; hh < 2; ++hh) {
+                            const int ch = 2 * cp + hh, c0 = cb + 32 * ch;
 #pragma unroll
-                        for (int u = 0; u < 16; u += 2) {
-                            const float4 w = *(const float4 *)(w2s + c0 + 2 * u);
-                            zp[(u >> 1) & 3] = fmaf(bf_lo(hp[16 * ch + u]), w.x, zp[(u >> 1) & 3]);
-                            zp[(u >> 1) & 3] = fmaf(bf_hi(hp[16 * ch + u]), w.y, zp[(u >> 1) & 3]);
-                            zp[(u >> 1) & 3] = fmaf(bf_lo(hp[16 * ch + u + 1]), w.z, zp[(u >> 1) & 3]);
-                            zp[(u >> 1) & 3] = fmaf(bf_hi(hp[16 * ch + u + 1]), w.w, zp[(u >> 1) & 3]);
+                            for (int u = 0; u < 16; ++u)
+                                hp[16 * ch + u] = sigmoid_half_bf2(
+                                    pack_bf16(__uint_as_float(zr2[hh][2 * u]), __uint_as_float(zr2[hh][2 * u + 1])));
+#pragma unroll
+                            for (int u = 0; u < 16; u += 2) {
+                                const float4 w = *(const float4 *)(w2s + c0 + 2 * u);
+                                zp[(u >> 1) & 3] = fmaf(bf_lo(hp[16 * ch + u]), w.x, zp[(u >> 1) & 3]);
+                                zp[(u >> 1) & 3] = fmaf(bf_hi(hp[16 * ch + u]), w.y, zp[(u >> 1) & 3]);
+                                zp[(u >> 1) & 3] = fmaf(bf_lo(hp[16 * ch + u + 1]), w.z, zp[(u >> 1) & 3]);
+                                zp[(u >> 1) & 3] = fmaf(bf_hi(hp[16 * ch + u + 1]), w.w, zp[(u >> 1) & 3]);
+                            }
+#pragma unroll
+                            for (int v = 0; v < 4; ++v)
+                                *(uint4 *)(sm + SM_HT + mnmajor_chunk(c0 + 8 * v, r)) =
+                                    make_uint4(hp[16 * ch + 4 * v], hp[16 * ch + 4 * v + 1], hp[16 * ch + 4 * v + 2],
+                                               hp[16 * ch + 4 * v + 3]);
                         }
-#pragma unroll
-                        for (int v = 0; v < 4; ++v)
-                            *(uint4 *)(sm + SM_HT + mnmajor_chunk(c0 + 8 * v, r)) =
-                                make_uint4(hp[16 * ch + 4 * v], hp[16 * ch + 4 * v + 1], hp[16 * ch + 4 * v + 2],
-                                           hp[16 * ch + 4 * v + 3]);
                     }
                     tc_fence_before();
                     mbar_arrive(BAR_Z1E);
@@ -332,6 +350,17 @@ __global__ void __launch_bounds__(NT, 1) k_tc_cluster(const __grid_constant__ CU
                                 st_async_v4(remote_addr(src, (uint32_t)cr), v, remote_addr(zbar, (uint32_t)cr));
                         }
                     }
+                    // while the shares travel: u = w2 h (1 - h) in bf16 pairs, in place
+#pragma unroll
+                    for (int ch = 0; ch < 16; ++ch) {
+                        const uint4 wv = *(const uint4 *)(w2b + cb + 8 * ch);
+                        const uint32_t wp[4] = {wv.x, wv.y, wv.z, wv.w};
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) {
+                            const uint32_t h = hp[4 * ch + v];
+                            hp[4 * ch + v] = hmul2(wp[v], hmul2(h, hfma2(h, BF2_NEG1, BF2_ONE)));
+                        }
+                    }
                     if (!mbar_wait(zbar, (tcount >> 1) & 1, abort)) { eok = false; break; }
                     // re-arm this parity for tile tcount + 2 (its shares can only be
                     // sent after every block has read this tile's)
@@ -348,22 +377,14 @@ __global__ void __launch_bounds__(NT, 1) k_tc_cluster(const __grid_constant__ CU
                     }
                     proxy_fence();
                     mbar_arrive(BAR_HF);
-                    // pass 2: d1 = d2 w2 h (1 - h) in bf16 pairs, written as d1^T
+                    // pass 2: d1 = d2 u in bf16 pairs, written as d1^T
                     if (!mbar_wait(BAR_DE, (de_use++ & 1) ^ 1, abort)) { eok = false; break; }
                     const uint32_t d2p = pack_bf16(d2, d2);
 #pragma unroll
-                    for (int ch = 0; ch < 16; ++ch) {
-                        const int c0 = cb + 8 * ch;
-                        const uint4 wv = *(const uint4 *)(w2b + c0);
-                        const uint32_t wp[4] = {wv.x, wv.y, wv.z, wv.w};
-                        uint32_t dk[4];
-#pragma unroll
-                        for (int v = 0; v < 4; ++v) {
-                            const uint32_t h = hp[4 * ch + v];
-                            dk[v] = hmul2(hmul2(wp[v], d2p), hmul2(h, hfma2(h, BF2_NEG1, BF2_ONE)));
-                        }
-                        *(uint4 *)(sm + SM_DT + mnmajor_chunk(c0, r)) = make_uint4(dk[0], dk[1], dk[2], dk[3]);
-                    }
+                    for (int ch = 0; ch < 16; ++ch)
+                        *(uint4 *)(sm + SM_DT + mnmajor_chunk(cb + 8 * ch, r)) =
+                            make_uint4(hmul2(hp[4 * ch], d2p), hmul2(hp[4 * ch + 1], d2p), hmul2(hp[4 * ch + 2], d2p),
+                                       hmul2(hp[4 * ch + 3], d2p));
                     if (half == 0) {
                         const int s = tcount % NSTAGE;   // the ones column of [X | 1]
                         *(__nv_bfloat16 *)(sm + SM_X + 16384 * s + kmajor_off(r, D)) = __float2bfloat16_rn(1.0f);
