@@ -3,12 +3,15 @@
 // output error, backpropagation, full-batch gradient descent, no momentum).
 //
 // Per tile of 128 rows of X (bf16, loaded by TMA into a 128-byte-swizzled tile):
-//   forward    Z1 = X W1^T           tcgen05.mma M = 128 rows, N = H, K = D,
-//                                    A = X tile (K-major), B = bf16 copy of W1
-//                                    (K-major), FP32 accumulator in tensor memory;
+//   forward    Z1 = X (W1/2)^T + 1 (b1/2)^T    tcgen05.mma M = 128 rows, N = H,
+//                                    K = D, A = X tile (K-major), B = bf16 copy
+//                                    of W1/2 (K-major), plus one K = 16 MMA of a
+//                                    ones column against b1/2; FP32 accumulator
+//                                    in tensor memory holds z1/2;
 //   epilogue   thread r of 4 warps owns row r (= tensor-memory lane r):
-//              h = sigmoid(z1 + b1), z2 = h w2 + b2, o = sigmoid(z2),
-//              d2 = c (o - y) o (1 - o), d1 = d2 w2 h (1 - h);
+//              h = sigmoid(z1) = 1/2 + tanh(z1/2)/2 in bf16 pairs, z2 = h w2 + b2
+//              (FP32), o = sigmoid(z2), d2 = c (o - y) o (1 - o),
+//              u = w2 h (1 - h) and d1 = d2 u in bf16 pairs;
 //              h and d1 go to shared memory as bf16, transposed on the fly
 //              (MN-major operand tiles), d2 to a small K-major operand;
 //   gradient   gW1 += d1^T X         M = 128 hidden units, N = 64, K = 128 rows,
@@ -23,7 +26,9 @@
 // Roles: warp 0 issues the TMA loads, warp 1 issues the MMAs (one thread each),
 // warps 2..9 run the epilogue: the two warps that share a tensor-memory lane
 // quarter take one half of the hidden columns each and add their halves of z2
-// through shared memory.  Every wait is bounded; on a timeout the block
+// through shared memory.  The gw2 MMA of a tile is issued as soon as h^T and
+// d2 are written and the gW1 MMA when d1^T is, so the next tile's first pass
+// only waits for the former.  Every wait is bounded; on a timeout the block
 // records MLP_ETIMEOUT, stops issuing, drains what it issued (again bounded),
 // frees its tensor memory and leaves.
 #include <mutex>
@@ -50,13 +55,17 @@ constexpr uint32_t SM_W1 = SM_X + NSTAGE * 16384;          // H x 128 B
 constexpr uint32_t SM_HT = SM_W1 + HMAX * 128;             // 4 x 16 KB (h^T)
 constexpr uint32_t SM_DT = SM_HT + 4 * 16384;              // 4 x 16 KB (d1^T)
 constexpr uint32_t SM_B3 = SM_DT + 4 * 16384;              // 4 KB (d2)
-constexpr uint32_t SM_B1 = SM_B3 + 4096;                   // fp32 b1
+constexpr uint32_t SM_ONES = SM_B3 + 4096;                 // 128 x 16 bf16, column 0 = 1
+constexpr uint32_t SM_B1T = SM_ONES + 4096;                // H x 16 bf16, column 0 = b1/2
+constexpr uint32_t SM_B1 = SM_B1T + HMAX * 32;             // fp32 b1
 constexpr uint32_t SM_W2 = SM_B1 + HMAX * 4;               // fp32 w2
-constexpr uint32_t SM_BAR = SM_W2 + HMAX * 4;              // mbarriers
+constexpr uint32_t SM_W2B = SM_W2 + HMAX * 4;              // bf16 w2
+constexpr uint32_t SM_BAR = SM_W2B + HMAX * 2;             // mbarriers
 constexpr uint32_t SM_MISC = SM_BAR + 256;                 // tmem slot, flags, reductions
 constexpr uint32_t SM_ZX = SM_MISC + 256;                  // z2 halves: 2 parities x 2 halves x 128 rows
 constexpr uint32_t SM_TOTAL = SM_ZX + 2 * 2 * 128 * 4;
 constexpr uint32_t SM_ALLOC = SM_TOTAL + 1024;             // + alignment slack
+static_assert(SM_ALLOC <= 227 * 1024, "shared memory");
 
 struct TcNet {
     const CUtensorMap *tmap;  // X: bf16 [n x D], box 64 x 128, 128-byte swizzle
@@ -87,28 +96,25 @@ __global__ void __launch_bounds__(NT, 1) k_tc_batched(TcArgs a) {
     const uint32_t sb = s32(sm);
     float *b1s = (float *)(sm + SM_B1);
     float *w2s = (float *)(sm + SM_W2);
+    __nv_bfloat16 *w2b = (__nv_bfloat16 *)(sm + SM_W2B);
     const uint32_t bar0 = sb + SM_BAR;
-    // mbarriers: full[2], empty[2], z1_full, z1_empty, a_full, a_empty, epoch_done, w_ready
+    // TMA -> MMA: FULL; MMA -> TMA: EMPTY; MMA -> epilogue: Z1F (forward done),
+    // HE (h^T, d2 read), DE (d1^T read), EPOCH; epilogue -> MMA: Z1E (Z1 read),
+    // HF (h^T, d2 written), DF (d1^T written), W (weights updated).
     const uint32_t BAR_FULL = bar0, BAR_EMPTY = bar0 + 16, BAR_Z1F = bar0 + 32, BAR_Z1E = bar0 + 40,
-                   BAR_AF = bar0 + 48, BAR_AE = bar0 + 56, BAR_EPOCH = bar0 + 64, BAR_W = bar0 + 72,
-                   BAR_DRAIN = bar0 + 80, BAR_EPI = bar0 + 88;
+                   BAR_HF = bar0 + 48, BAR_HE = bar0 + 56, BAR_DF = bar0 + 64, BAR_DE = bar0 + 72,
+                   BAR_EPOCH = bar0 + 80, BAR_W = bar0 + 88, BAR_DRAIN = bar0 + 96, BAR_EPI = bar0 + 104;
     uint32_t *tmem_slot = (uint32_t *)(sm + SM_MISC);
     volatile int *abort = (volatile int *)(sm + SM_MISC + 16);
     float *red = (float *)(sm + SM_MISC + 64);     // 4 warps x (sse, gb2)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int D = a.D;
+    const uint32_t bars[12] = {BAR_FULL, BAR_FULL + 8, BAR_EMPTY, BAR_EMPTY + 8, BAR_Z1F, BAR_Z1E,
+                               BAR_HF,   BAR_HE,       BAR_DF,    BAR_DE,        BAR_EPOCH, BAR_W};
+    const uint32_t counts[12] = {1, 1, 1, 1, 1, NEPI_T, NEPI_T, 1, NEPI_T, 1, 1, NEPI_T};
 
     if (tid == 0) {
-        for (int s = 0; s < NSTAGE; ++s) {
-            mbar_init(BAR_FULL + 8 * s, 1);
-            mbar_init(BAR_EMPTY + 8 * s, 1);
-        }
-        mbar_init(BAR_Z1F, 1);
-        mbar_init(BAR_Z1E, NEPI_T);
-        mbar_init(BAR_AF, NEPI_T);
-        mbar_init(BAR_AE, 1);
-        mbar_init(BAR_EPOCH, 1);
-        mbar_init(BAR_W, NEPI_T);
+        for (int i = 0; i < 12; ++i) mbar_init(bars[i], counts[i]);
         mbar_init(BAR_DRAIN, 1);
         mbar_init(BAR_EPI, NEPI_T);
         *abort = 0;
@@ -118,8 +124,12 @@ __global__ void __launch_bounds__(NT, 1) k_tc_batched(TcArgs a) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(s32(tmem_slot)));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
-    // zero the d2 operand once (rows n = 1..15 stay zero)
-    for (int i = tid; i < 4096 / 4; i += NT) ((uint32_t *)(sm + SM_B3))[i] = 0u;
+    // constant operands: the d2 tile and b1 tile zero (only column 0 is ever
+    // written), the ones tile with column 0 = 1
+    for (int i = tid; i < (4096 + 4096 + HMAX * 32) / 4; i += NT) ((uint32_t *)(sm + SM_B3))[i] = 0u;
+    __syncthreads();
+    for (int row = tid; row < TR; row += NT)
+        *(__nv_bfloat16 *)(sm + SM_ONES + k16_off(row, 0)) = __float2bfloat16_rn(1.0f);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -136,15 +146,18 @@ __global__ void __launch_bounds__(NT, 1) k_tc_batched(TcArgs a) {
         float *P = nd.params;
         const int HD = H * D;
 
-        // ---- weights into shared memory: bf16 W1 (swizzled, zero padded), b1, w2
+        // ---- weights into shared memory: bf16 W1/2 (swizzled, zero padded),
+        // b1/2 as the bias operand, b1, w2 (FP32) and w2 (bf16)
         for (int i = tid; i < H * 64; i += NT) {
             const int j = i >> 6, k = i & 63;
             const float v = (k < D) ? P[j * D + k] : 0.f;
-            *(__nv_bfloat16 *)(sm + SM_W1 + kmajor_off(j, k)) = __float2bfloat16_rn(v);
+            *(__nv_bfloat16 *)(sm + SM_W1 + kmajor_off(j, k)) = __float2bfloat16_rn(0.5f * v);
         }
         for (int j = tid; j < H; j += NT) {
             b1s[j] = P[HD + j];
             w2s[j] = P[HD + H + j];
+            w2b[j] = __float2bfloat16_rn(w2s[j]);
+            *(__nv_bfloat16 *)(sm + SM_B1T + k16_off(j, 0)) = __float2bfloat16_rn(0.5f * b1s[j]);
         }
         proxy_fence();
         tc_fence_before();
@@ -161,18 +174,14 @@ __global__ void __launch_bounds__(NT, 1) k_tc_batched(TcArgs a) {
         // Barrier phase counters restart for every net: the previous net's
         // waits were all completed, so re-initialising is safe after a sync.
         if (tid == 0) {
-            for (int s = 0; s < NSTAGE; ++s) {
-                asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(BAR_FULL + 8 * s));
-                asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(BAR_EMPTY + 8 * s));
-                mbar_init(BAR_FULL + 8 * s, 1);
-                mbar_init(BAR_EMPTY + 8 * s, 1);
+            for (int i = 0; i < 12; ++i) {
+                asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(bars[i]));
+                mbar_init(bars[i], counts[i]);
             }
-            const uint32_t others[8] = {BAR_Z1F, BAR_Z1E, BAR_AF, BAR_AE, BAR_EPOCH, BAR_W, BAR_DRAIN, BAR_EPI};
-            const uint32_t counts[8] = {1, NEPI_T, NEPI_T, 1, 1, NEPI_T, 1, NEPI_T};
-            for (int q = 0; q < 8; ++q) {
-                asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(others[q]));
-                mbar_init(others[q], counts[q]);
-            }
+            asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(BAR_DRAIN));
+            mbar_init(BAR_DRAIN, 1);
+            asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(BAR_EPI));
+            mbar_init(BAR_EPI, NEPI_T);
             asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         }
         __syncthreads();
@@ -199,46 +208,51 @@ __global__ void __launch_bounds__(NT, 1) k_tc_batched(TcArgs a) {
                 const uint32_t id_fwd = idesc_bf16(128, H, 0, 0);
                 const uint32_t id_gw1 = idesc_bf16(128, 64, 1, 1);
                 const uint32_t id_gw2 = idesc_bf16(128, 16, 1, 0);
-                int it = 0, z1e_use = 0, af_use = 0;
-                auto grad = [&](int itp, int first) {
-                    const int s = itp % NSTAGE;
+                int it = 0, itf = 0, z1e_use = 0, hf_use = 0, df_use = 0;
+                // Z1 = X (W1/2)^T + 1 (b1/2)^T for tile itf once its X tile has landed
+                // and the epilogue has read the previous Z1
+                auto forward = [&]() -> bool {
+                    const int s = itf % NSTAGE;
+                    if (!mbar_wait(BAR_FULL + 8 * s, (itf / NSTAGE) & 1, abort)) return false;
+                    if (!mbar_wait(BAR_Z1E, (z1e_use++ & 1) ^ 1, abort)) return false;
+                    tc_fence_after();
                     const uint32_t xs = sb + SM_X + 16384 * s;
-                    for (int hb = 0; hb < H / 128; ++hb)
-                        for (int kk = 0; kk < TR / 16; ++kk) {
-                            const uint64_t ad = sdesc(sb + SM_DT + hb * 2 * 16384 + kk * 2048, 16384, 1024, 2);
-                            const uint64_t bd = sdesc(xs + kk * 2048, 16384, 1024, 2);
-                            mma_bf16(tmem + TM_GW1 + 64 * hb, ad, bd, id_gw1, (first && kk == 0) ? 0u : 1u);
-                            const uint64_t hd = sdesc(sb + SM_HT + hb * 2 * 16384 + kk * 2048, 16384, 1024, 2);
-                            const uint64_t d3 = sdesc(sb + SM_B3 + kk * 256, 128, 2048, 0);
-                            mma_bf16(tmem + TM_GW2 + 16 * hb, hd, d3, id_gw2, (first && kk == 0) ? 0u : 1u);
-                        }
-                    mma_commit(BAR_AE);
-                    mma_commit(BAR_EMPTY + 8 * s);
+                    for (int ks = 0; ks < Dk / 16; ++ks)
+                        mma_bf16(tmem + TM_Z1, sdesc(xs + ks * 32, 16, 1024, 2), sdesc(sb + SM_W1 + ks * 32, 16, 1024, 2),
+                                 id_fwd, ks > 0 ? 1u : 0u);
+                    mma_bf16(tmem + TM_Z1, sdesc(sb + SM_ONES, 128, 256, 0), sdesc(sb + SM_B1T, 128, 256, 0), id_fwd, 1u);
+                    mma_commit(BAR_Z1F);
+                    ++itf;
+                    return true;
                 };
                 bool ok = true;
                 for (int e = 0; e < a.epochs && ok; ++e) {
                     if (e > 0 && !mbar_wait(BAR_W, (e - 1) & 1, abort)) { ok = false; break; }
                     tc_fence_after();
+                    if (!forward()) { ok = false; break; }
                     for (int t = 0; t < T; ++t, ++it) {
+                        if (t + 1 < T && !forward()) { ok = false; break; }
                         const int s = it % NSTAGE;
-                        if (!mbar_wait(BAR_FULL + 8 * s, (it / NSTAGE) & 1, abort)) { ok = false; break; }
-                        if (!mbar_wait(BAR_Z1E, (z1e_use++ & 1) ^ 1, abort)) { ok = false; break; }
-                        tc_fence_after();
                         const uint32_t xs = sb + SM_X + 16384 * s;
-                        for (int ks = 0; ks < Dk / 16; ++ks)
-                            mma_bf16(tmem + TM_Z1, sdesc(xs + ks * 32, 16, 1024, 2),
-                                     sdesc(sb + SM_W1 + ks * 32, 16, 1024, 2), id_fwd, ks > 0 ? 1u : 0u);
-                        mma_commit(BAR_Z1F);
-                        if (t > 0) {
-                            if (!mbar_wait(BAR_AF, af_use++ & 1, abort)) { ok = false; break; }
-                            tc_fence_after();
-                            grad(it - 1, t == 1);
-                        }
+                        // gw2 += h^T d2 as soon as h^T and d2 are written
+                        if (!mbar_wait(BAR_HF, hf_use++ & 1, abort)) { ok = false; break; }
+                        tc_fence_after();
+                        for (int hb = 0; hb < H / 128; ++hb)
+                            for (int kk = 0; kk < TR / 16; ++kk)
+                                mma_bf16(tmem + TM_GW2 + 16 * hb, sdesc(sb + SM_HT + hb * 32768 + kk * 2048, 16384, 1024, 2),
+                                         sdesc(sb + SM_B3 + kk * 256, 128, 2048, 0), id_gw2, (t > 0 || kk > 0) ? 1u : 0u);
+                        mma_commit(BAR_HE);
+                        // [gW1 | gb1] += d1^T [X | 1]
+                        if (!mbar_wait(BAR_DF, df_use++ & 1, abort)) { ok = false; break; }
+                        tc_fence_after();
+                        for (int hb = 0; hb < H / 128; ++hb)
+                            for (int kk = 0; kk < TR / 16; ++kk)
+                                mma_bf16(tmem + TM_GW1 + 64 * hb, sdesc(sb + SM_DT + hb * 32768 + kk * 2048, 16384, 1024, 2),
+                                         sdesc(xs + kk * 2048, 16384, 1024, 2), id_gw1, (t > 0 || kk > 0) ? 1u : 0u);
+                        mma_commit(BAR_DE);
+                        mma_commit(BAR_EMPTY + 8 * s);
                     }
                     if (!ok) break;
-                    if (!mbar_wait(BAR_AF, af_use++ & 1, abort)) { ok = false; break; }
-                    tc_fence_after();
-                    grad(it - 1, T == 1);
                     mma_commit(BAR_EPOCH);
                 }
                 // drain every MMA issued before tensor memory is released
@@ -252,8 +266,9 @@ __global__ void __launch_bounds__(NT, 1) k_tc_batched(TcArgs a) {
             const int r = q * 32 + lane;            // row within the tile / lane
             const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
             const int cw = H / 2, cb = half * cw;   // this thread's columns [cb, cb + cw)
+            const int nch = cw / 32;                // 32-column chunks: 2 (H = 128) or 4
             float *zx = (float *)(sm + SM_ZX);
-            int z1f_use = 0, ae_use = 0, epi_use = 0;
+            int z1f_use = 0, he_use = 0, de_use = 0, epi_use = 0;
             bool ok = true;
             // Barrier of the epilogue threads with a bounded wait (an mbarrier,
             // so that a block that aborts cannot leave it hanging).
@@ -271,68 +286,81 @@ __global__ void __launch_bounds__(NT, 1) k_tc_batched(TcArgs a) {
                     const float yv = y_next;
                     if (row + TR < n) y_next = nd.y[row + TR];
                     if (!mbar_wait(BAR_Z1F, z1f_use++ & 1, abort)) { ok = false; break; }
-                    // the previous tile's gradient MMAs must be done with h^T, d1^T, d2
-                    if (!mbar_wait(BAR_AE, (ae_use++ & 1) ^ 1, abort)) { ok = false; break; }
+                    // the previous tile's gw2 MMA must be done with h^T and d2
+                    if (!mbar_wait(BAR_HE, (he_use++ & 1) ^ 1, abort)) { ok = false; break; }
                     tc_fence_after();
-                    // pass 1: h = sigmoid(z1 + b1) -> h^T (bf16), half of z2; the
-                    // next 32 columns are loaded from tensor memory while these are
-                    // processed, and z2 is summed in four independent chains
+                    // pass 1: h = sigmoid(z1) in bf16 pairs -> h^T, this half's
+                    // share of z2 = h w2 in FP32
+                    uint32_t hp[64];
                     float zp[4] = {0.f, 0.f, 0.f, 0.f};
-                    uint32_t zr[32];
-                    tmem_ld32_async(lane_base + TM_Z1 + cb, zr);
-                    tmem_wait_regs(zr);
-                    for (int c0 = cb; c0 < cb + cw; c0 += 32) {
+#pragma unroll
+                    for (int ch = 0; ch < 4; ++ch) {
+                        if (ch >= nch) break;
+                        const int c0 = cb + 32 * ch;
                         float z[32];
+                        tmem_ld32(lane_base + TM_Z1 + c0, z);
 #pragma unroll
-                        for (int i = 0; i < 32; ++i) z[i] = __uint_as_float(zr[i]);
-                        if (c0 + 32 < cb + cw) tmem_ld32_async(lane_base + TM_Z1 + c0 + 32, zr);
-                        uint32_t pk[16];
+                        for (int u = 0; u < 16; ++u) hp[16 * ch + u] = sigmoid_half_bf2(pack_bf16(z[2 * u], z[2 * u + 1]));
 #pragma unroll
-                        for (int i = 0; i < 32; i += 2) {
-                            const float h0 = sigmoid_bf(z[i] + b1s[c0 + i]);
-                            const float h1 = sigmoid_bf(z[i + 1] + b1s[c0 + i + 1]);
-                            zp[(i >> 1) & 3] = fmaf(h0, w2s[c0 + i], zp[(i >> 1) & 3]);
-                            zp[(i >> 1) & 3] = fmaf(h1, w2s[c0 + i + 1], zp[(i >> 1) & 3]);
-                            pk[i >> 1] = pack_bf16(h0, h1);
+                        for (int u = 0; u < 16; u += 2) {
+                            const float4 w = *(const float4 *)(w2s + c0 + 2 * u);
+                            zp[(u >> 1) & 3] = fmaf(bf_lo(hp[16 * ch + u]), w.x, zp[(u >> 1) & 3]);
+                            zp[(u >> 1) & 3] = fmaf(bf_hi(hp[16 * ch + u]), w.y, zp[(u >> 1) & 3]);
+                            zp[(u >> 1) & 3] = fmaf(bf_lo(hp[16 * ch + u + 1]), w.z, zp[(u >> 1) & 3]);
+                            zp[(u >> 1) & 3] = fmaf(bf_hi(hp[16 * ch + u + 1]), w.w, zp[(u >> 1) & 3]);
                         }
 #pragma unroll
                         for (int v = 0; v < 4; ++v)
                             *(uint4 *)(sm + SM_HT + mnmajor_chunk(c0 + 8 * v, r)) =
-                                make_uint4(pk[4 * v], pk[4 * v + 1], pk[4 * v + 2], pk[4 * v + 3]);
-                        tmem_wait_regs(zr);
+                                make_uint4(hp[16 * ch + 4 * v], hp[16 * ch + 4 * v + 1], hp[16 * ch + 4 * v + 2],
+                                           hp[16 * ch + 4 * v + 3]);
                     }
                     tc_fence_before();
                     mbar_arrive(BAR_Z1E);  // Z1 in tensor memory may be overwritten
+                    // the two halves' shares of z2 meet in shared memory; while the
+                    // other half arrives: u = w2 h (1 - h) in bf16 pairs, in place
                     float *zxp = zx + (tcount & 1) * 256;
                     zxp[half * 128 + r] = (zp[0] + zp[1]) + (zp[2] + zp[3]);
-                    if (!epi_sync()) { ok = false; break; }
+                    mbar_arrive(BAR_EPI);
+#pragma unroll
+                    for (int ch = 0; ch < 16; ++ch) {
+                        if (ch >= 4 * nch) break;
+                        const uint4 wv = *(const uint4 *)(w2b + cb + 8 * ch);
+                        const uint32_t wp[4] = {wv.x, wv.y, wv.z, wv.w};
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) {
+                            const uint32_t h = hp[4 * ch + v];
+                            hp[4 * ch + v] = hmul2(wp[v], hmul2(h, hfma2(h, BF2_NEG1, BF2_ONE)));
+                        }
+                    }
+                    if (!mbar_wait(BAR_EPI, epi_use++ & 1, abort)) { ok = false; break; }
                     const float o = sigmoid_bf(zxp[r] + zxp[128 + r] + b2);
                     const float err = o - yv;
                     const float d2 = valid ? c * err * o * (1.0f - o) : 0.f;
                     if (half == 0) {
                         if (valid) sse = fmaf(err, err, sse);
                         gb2s += d2;
-                        // d2 operand (n = 0, k = r) and the ones column of the X tile
                         *(__nv_bfloat16 *)(sm + SM_B3 + (r & 7) * 2 + (r >> 3) * 128) = __float2bfloat16_rn(d2);
-                        const int s = tcount % NSTAGE;
-                        *(__nv_bfloat16 *)(sm + SM_X + 16384 * s + kmajor_off(r, D)) = __float2bfloat16_rn(1.0f);
-                    }
-                    // pass 2: d1 = d2 w2 h (1 - h) -> d1^T (bf16)
-                    for (int c0 = cb; c0 < cb + cw; c0 += 8) {
-                        const uint4 hv = *(const uint4 *)(sm + SM_HT + mnmajor_chunk(c0, r));
-                        const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w};
-                        uint32_t dk[4];
-#pragma unroll
-                        for (int v = 0; v < 4; ++v) {
-                            const float h0 = bf_lo(hw[v]), h1 = bf_hi(hw[v]);
-                            const float d10 = d2 * w2s[c0 + 2 * v] * (h0 - h0 * h0);
-                            const float d11 = d2 * w2s[c0 + 2 * v + 1] * (h1 - h1 * h1);
-                            dk[v] = pack_bf16(d10, d11);
-                        }
-                        *(uint4 *)(sm + SM_DT + mnmajor_chunk(c0, r)) = make_uint4(dk[0], dk[1], dk[2], dk[3]);
                     }
                     proxy_fence();
-                    mbar_arrive(BAR_AF);
+                    mbar_arrive(BAR_HF);
+                    // pass 2: d1 = d2 u in bf16 pairs -> d1^T, once the previous
+                    // tile's gW1 MMA has read d1^T
+                    if (!mbar_wait(BAR_DE, (de_use++ & 1) ^ 1, abort)) { ok = false; break; }
+                    const uint32_t d2p = pack_bf16(d2, d2);
+#pragma unroll
+                    for (int ch = 0; ch < 16; ++ch) {
+                        if (ch >= 4 * nch) break;
+                        *(uint4 *)(sm + SM_DT + mnmajor_chunk(cb + 8 * ch, r)) =
+                            make_uint4(hmul2(hp[4 * ch], d2p), hmul2(hp[4 * ch + 1], d2p), hmul2(hp[4 * ch + 2], d2p),
+                                       hmul2(hp[4 * ch + 3], d2p));
+                    }
+                    if (half == 0) {
+                        const int s = tcount % NSTAGE;   // the ones column of [X | 1]
+                        *(__nv_bfloat16 *)(sm + SM_X + 16384 * s + kmajor_off(r, D)) = __float2bfloat16_rn(1.0f);
+                    }
+                    proxy_fence();
+                    mbar_arrive(BAR_DF);
                 }
                 if (!ok) break;
                 // ---- end of epoch: reductions and the update
@@ -355,21 +383,32 @@ __global__ void __launch_bounds__(NT, 1) k_tc_batched(TcArgs a) {
                 if (half < H / 128) {
                     const int hb = half;
                     const int j = hb * 128 + r;  // hidden unit = lane
-                    float g[64];
-                    tmem_ld32(lane_base + TM_GW1 + 64 * hb, *reinterpret_cast<float(*)[32]>(&g[0]));
-                    tmem_ld32(lane_base + TM_GW1 + 64 * hb + 32, *reinterpret_cast<float(*)[32]>(&g[32]));
                     const float gw2 = tmem_ld1(lane_base + TM_GW2 + 16 * hb);
-                    for (int k = 0; k < D; ++k) {
-                        const float w = P[j * D + k] - a.lr * g[k];
-                        P[j * D + k] = w;
-                        *(__nv_bfloat16 *)(sm + SM_W1 + kmajor_off(j, k)) = __float2bfloat16_rn(w);
+                    const float gb1 = tmem_ld1(lane_base + TM_GW1 + 64 * hb + D);   // the ones column
+#pragma unroll
+                    for (int c16 = 0; c16 < 64; c16 += 16) {
+                        if (c16 >= D) break;
+                        float g[16], w[16];
+                        tmem_ld16(lane_base + TM_GW1 + 64 * hb + c16, g);
+#pragma unroll
+                        for (int u = 0; u < 16; ++u)
+                            if (c16 + u < D) w[u] = P[j * D + c16 + u];
+#pragma unroll
+                        for (int u = 0; u < 16; ++u)
+                            if (c16 + u < D) {
+                                w[u] -= a.lr * g[u];
+                                P[j * D + c16 + u] = w[u];
+                                *(__nv_bfloat16 *)(sm + SM_W1 + kmajor_off(j, c16 + u)) = __float2bfloat16_rn(0.5f * w[u]);
+                            }
                     }
-                    const float nb1 = b1s[j] - a.lr * g[D];
+                    const float nb1 = b1s[j] - a.lr * gb1;
                     const float nw2 = w2s[j] - a.lr * gw2;
                     P[HD + j] = nb1;
                     P[HD + H + j] = nw2;
                     b1s[j] = nb1;
                     w2s[j] = nw2;
+                    w2b[j] = __float2bfloat16_rn(nw2);
+                    *(__nv_bfloat16 *)(sm + SM_B1T + k16_off(j, 0)) = __float2bfloat16_rn(0.5f * nb1);
                 }
                 b2 -= a.lr * gb2;
                 if (half == 0 && r == 0) {
