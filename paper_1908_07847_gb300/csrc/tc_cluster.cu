@@ -299,37 +299,29 @@ __global__ void __launch_bounds__(NT, 1) k_tc_cluster(const __grid_constant__ CU
                     if (!mbar_wait(BAR_HE, (he_use++ & 1) ^ 1, abort)) { eok = false; break; }
                     tc_fence_after();
                     // pass 1: h = sigmoid(z1) in bf16 pairs (written as h^T), this
-                    // block's share of z2 = h w2 in FP32; two 32-column loads in flight
+                    // block's share of z2 = h w2 with FP32 accumulation
                     uint32_t hp[64];
                     float zp[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-                    for (int cp = 0; cp < 2; ++cp) {
-                        uint32_t zr2[2][32];
-                        tmem_ld32_async(lane_base + TM_Z1 + cb + 64 * cp, zr2[0]);
-                        tmem_ld32_async(lane_base + TM_Z1 + cb + 64 * cp + 32, zr2[1]);
-                        tmem_wait_regs(zr2[0]);
-                        tmem_tie_regs(zr2[1]);
+                    for (int ch = 0; ch < 4; ++ch) {
+                        const int c0 = cb + 32 * ch;
+                        float z[32];
+                        tmem_ld32(lane_base + TM_Z1 + c0, z);
 #pragma unroll
-                        for (int hh = 0; hh < 2; ++hh) {
-                            const int ch = 2 * cp + hh, c0 = cb + 32 * ch;
+                        for (int u = 0; u < 16; ++u) hp[16 * ch + u] = sigmoid_half_bf2(pack_bf16(z[2 * u], z[2 * u + 1]));
 #pragma unroll
-                            for (int u = 0; u < 16; ++u)
-                                hp[16 * ch + u] = sigmoid_half_bf2(
-                                    pack_bf16(__uint_as_float(zr2[hh][2 * u]), __uint_as_float(zr2[hh][2 * u + 1])));
-#pragma unroll
-                            for (int u = 0; u < 16; u += 2) {
-                                const float4 w = *(const float4 *)(w2s + c0 + 2 * u);
-                                zp[(u >> 1) & 3] = fmaf(bf_lo(hp[16 * ch + u]), w.x, zp[(u >> 1) & 3]);
-                                zp[(u >> 1) & 3] = fmaf(bf_hi(hp[16 * ch + u]), w.y, zp[(u >> 1) & 3]);
-                                zp[(u >> 1) & 3] = fmaf(bf_lo(hp[16 * ch + u + 1]), w.z, zp[(u >> 1) & 3]);
-                                zp[(u >> 1) & 3] = fmaf(bf_hi(hp[16 * ch + u + 1]), w.w, zp[(u >> 1) & 3]);
-                            }
-#pragma unroll
-                            for (int v = 0; v < 4; ++v)
-                                *(uint4 *)(sm + SM_HT + mnmajor_chunk(c0 + 8 * v, r)) =
-                                    make_uint4(hp[16 * ch + 4 * v], hp[16 * ch + 4 * v + 1], hp[16 * ch + 4 * v + 2],
-                                               hp[16 * ch + 4 * v + 3]);
+                        for (int u = 0; u < 16; u += 4) {
+                            const uint4 w = *(const uint4 *)(w2b + c0 + 2 * u);
+                            zp[0] = dot2_bf16(hp[16 * ch + u], w.x, zp[0]);
+                            zp[1] = dot2_bf16(hp[16 * ch + u + 1], w.y, zp[1]);
+                            zp[2] = dot2_bf16(hp[16 * ch + u + 2], w.z, zp[2]);
+                            zp[3] = dot2_bf16(hp[16 * ch + u + 3], w.w, zp[3]);
                         }
+#pragma unroll
+                        for (int v = 0; v < 4; ++v)
+                            *(uint4 *)(sm + SM_HT + mnmajor_chunk(c0 + 8 * v, r)) =
+                                make_uint4(hp[16 * ch + 4 * v], hp[16 * ch + 4 * v + 1], hp[16 * ch + 4 * v + 2],
+                                           hp[16 * ch + 4 * v + 3]);
                     }
                     tc_fence_before();
                     mbar_arrive(BAR_Z1E);

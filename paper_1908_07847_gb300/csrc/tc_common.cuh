@@ -201,6 +201,16 @@ __device__ __forceinline__ uint32_t hmul2(uint32_t a, uint32_t b) {
     asm("mul.rn.bf16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
     return d;
 }
+// acc + a.lo b.lo + a.hi b.hi with bf16 products accumulated in FP32 (the
+// mixed-precision fma of sm_100 and later).
+__device__ __forceinline__ float dot2_bf16(uint32_t a, uint32_t b, float acc) {
+    float d;
+    asm("{\n\t.reg .b16 al, ah, bl, bh;\n\tmov.b32 {al, ah}, %1;\n\tmov.b32 {bl, bh}, %2;\n\t"
+        "fma.rn.f32.bf16 %0, al, bl, %3;\n\tfma.rn.f32.bf16 %0, ah, bh, %0;\n\t}"
+        : "=f"(d)
+        : "r"(a), "r"(b), "f"(acc));
+    return d;
+}
 // sigmoid of a pair given half its argument: 1/2 + tanh(x/2)/2.
 __device__ __forceinline__ uint32_t sigmoid_half_bf2(uint32_t xhalf) { return hfma2(tanh_bf2(xhalf), BF2_HALF, BF2_HALF); }
 

@@ -302,12 +302,12 @@ __global__ void __launch_bounds__(NT, 1) k_tc_batched(TcArgs a) {
 #pragma unroll
                         for (int u = 0; u < 16; ++u) hp[16 * ch + u] = sigmoid_half_bf2(pack_bf16(z[2 * u], z[2 * u + 1]));
 #pragma unroll
-                        for (int u = 0; u < 16; u += 2) {
-                            const float4 w = *(const float4 *)(w2s + c0 + 2 * u);
-                            zp[(u >> 1) & 3] = fmaf(bf_lo(hp[16 * ch + u]), w.x, zp[(u >> 1) & 3]);
-                            zp[(u >> 1) & 3] = fmaf(bf_hi(hp[16 * ch + u]), w.y, zp[(u >> 1) & 3]);
-                            zp[(u >> 1) & 3] = fmaf(bf_lo(hp[16 * ch + u + 1]), w.z, zp[(u >> 1) & 3]);
-                            zp[(u >> 1) & 3] = fmaf(bf_hi(hp[16 * ch + u + 1]), w.w, zp[(u >> 1) & 3]);
+                        for (int u = 0; u < 16; u += 4) {
+                            const uint4 w = *(const uint4 *)(w2b + c0 + 2 * u);
+                            zp[0] = dot2_bf16(hp[16 * ch + u], w.x, zp[0]);
+                            zp[1] = dot2_bf16(hp[16 * ch + u + 1], w.y, zp[1]);
+                            zp[2] = dot2_bf16(hp[16 * ch + u + 2], w.z, zp[2]);
+                            zp[3] = dot2_bf16(hp[16 * ch + u + 3], w.w, zp[3]);
                         }
 #pragma unroll
                         for (int v = 0; v < 4; ++v)
