@@ -154,6 +154,22 @@ class ClockSampler:
 
 # ------------------------------------------------------------- our arm ------
 
+def unit_rates():
+    """Measured device rates (instructions/s) of the FP32 FMA pipe and of the
+    special-function unit for tanh and exp2, from the library's diagnostic."""
+    from paper_1908_07847_gb300 import binding as B
+    ffma, tanh, ex2 = B.mlp_unit_rates()
+    return {"ffma_tflops": 2 * ffma / 1e12, "tanh_per_s": tanh, "ex2_per_s": ex2}
+
+
+def sfu_roofline(sigmoids_per_launch, launch_s, rates):
+    """Sigmoids per second against the measured tanh rate of the SFU (the bf16
+    paths evaluate every sigmoid as one tanh, two per bf16x2 instruction at the
+    same value rate)."""
+    got = sigmoids_per_launch / launch_s
+    return {"achieved_per_s": got, "peak_per_s": rates["tanh_per_s"], "frac": got / rates["tanh_per_s"],
+            "peak_basis": "tanh.approx rate measured by mlp_unit_rates on this device"}
+
 def traffic_from_profile():
     """DRAM bytes per launch of the fused kernel from the committed ncu summary,
     if it was taken on the current kernel source; else None."""
@@ -202,6 +218,7 @@ def run_ours(args, rank, world, local):
         return [s.elapsed_time(e) * 1e-3 for s, e in ev]
 
     from paper_1908_07847_gb300 import autotune
+    rates = unit_rates()
     rows, _ = autotune.tune_fused(Xd, yd, D_IN, H_HID, N_ROWS)   # untimed; cached per device and shape
     h = B.mlp_create(D_IN, H_HID, LR, 1, B.MLP_FP32, B.MLP_ACT_SIGMOID)
     B.mlp_set_rows_per_block(h, rows)
@@ -266,6 +283,7 @@ def run_ours(args, rank, world, local):
                      "frac": achieved / peak, "traffic": traffic_from_profile(),
                      "kernel": "k_fused_train<36,2,sigmoid>",
                      "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (FFMA, derived)",
+                     "ffma_measured_tflops": rates["ffma_tflops"],
                      "flops_per_launch": FLOPS_PER_SAMPLE * N_ROWS},
         "gpu_launches": args.steps,
         "clocks": clocks,
@@ -504,6 +522,7 @@ def run_c3(args, rank, world, local):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream().cuda_stream
     X, y, W = c3_inputs(dev, 1908 + rank)
+    rates = unit_rates()
     h = B.mlp_create(C3_D, C3_H, LR, 1, B.MLP_BF16, B.MLP_ACT_SIGMOID)
     B.mlp_set_weights(h, *W)
     loss = torch.zeros(1, dtype=torch.float64, device=dev)
@@ -560,7 +579,8 @@ def run_c3(args, rank, world, local):
                 "call": "mlp_train_host (pinned host X, y in; loss out)"},
         "roofline": {"bound": "tensor", "achieved": mma_flops / launch_s / 1e12, "peak": peak, "unit": "TFLOP/s",
                      "frac": mma_flops / launch_s / 1e12 / peak, "traffic": None, "kernel": "k_tc_cluster",
-                     "peak_basis": "bf16_tflops_sustained of measured", "flops_per_launch": mma_flops},
+                     "peak_basis": "bf16_tflops_sustained of measured", "flops_per_launch": mma_flops,
+                     "sfu": sfu_roofline(float(C3_N) * (C3_H + 1), launch_s, rates)},
         "gpu_launches": args.steps, "clocks": clk.summary(),
     }
     if rank == 0:
@@ -582,6 +602,7 @@ def run_c4(args, rank, world, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream().cuda_stream
+    rates = unit_rates()
     seed = 4 + rank
     _, ns = I.batched_shapes(seed, C4_NETS, (C4_H, C4_H), (4096, 16384))
     offs = np.concatenate([[0], np.cumsum(ns)])
@@ -648,7 +669,8 @@ def run_c4(args, rank, world, local):
                    "l2": "inputs (1 GB of bf16 X) larger than L2; L2 also flushed between timed steps"},
         "roofline": {"bound": "tensor", "achieved": mma_flops / launch_s / 1e12, "peak": peak, "unit": "TFLOP/s",
                      "frac": mma_flops / launch_s / 1e12 / peak, "traffic": None, "kernel": "k_tc_batched",
-                     "peak_basis": "bf16_tflops_sustained of measured", "flops_per_launch": mma_flops},
+                     "peak_basis": "bf16_tflops_sustained of measured", "flops_per_launch": mma_flops,
+                     "sfu": sfu_roofline(float(ns.sum()) * C4_EPOCHS * (C4_H + 1), launch_s, rates)},
         "gpu_launches": args.steps, "clocks": clk.summary(),
     }
     if rank == 0:

@@ -257,6 +257,14 @@ mlp_status mlp_train_fused_noalloc(int32_t act, int32_t D, int32_t H, int64_t n,
                                    int64_t minibatch, double *loss_hist,
                                    int32_t *status_out, void *stream);
 
+/* Diagnostic, not part of the method: measured rates of the FP32 FMA pipe and
+ * of the special-function unit for tanh.approx.f32 and ex2.approx.f32, in
+ * instructions per second over the whole current device (CUDA-event timed
+ * register-only kernels, about 10 ms).  The benchmark states its ALU and SFU
+ * roofline peaks from these.  MLP_EINVAL for a NULL pointer, MLP_ENOMEM /
+ * MLP_ECUDA if the 4 x SMs x 512-word buffer or a launch fails. */
+mlp_status mlp_unit_rates(double *ffma_per_s, double *tanh_per_s, double *ex2_per_s);
+
 /* Message of the last failure on the calling thread ("" if none). */
 const char *mlp_last_error(void);
 

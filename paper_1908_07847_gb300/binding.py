@@ -26,7 +26,7 @@ EXPORTS = [
     "mlp_train_host", "mlp_predict", "mlp_check", "mlp_workspace_bytes", "mlp_forward_w",
     "mlp_backward_w", "mlp_debug_skip_block", "mlp_set_rows_per_block", "mlp_batch_train",
     "mlp_batch_create", "mlp_batch_run", "mlp_batch_check", "mlp_batch_destroy", "mlp_train_fused_noalloc",
-    "mlp_last_error", "mlp_version",
+    "mlp_unit_rates", "mlp_last_error", "mlp_version",
 ]
 
 
@@ -92,6 +92,7 @@ def lib():
             "mlp_train_fused_noalloc": (S, [I32, I32, I32, I64, V, V, V, F, I32, I32, I64, V, V, V]),
             "mlp_last_error": (ctypes.c_char_p, []),
             "mlp_version": (ctypes.c_char_p, []),
+            "mlp_unit_rates": (S, [ctypes.POINTER(ctypes.c_double)] * 3),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -246,3 +247,11 @@ def mlp_last_error():
 
 def mlp_version():
     return lib().mlp_version().decode()
+
+
+def mlp_unit_rates():
+    """(FP32 FMA, tanh.approx.f32, ex2.approx.f32) instructions per second,
+    measured on the current device."""
+    v = [ctypes.c_double() for _ in range(3)]
+    _ck(lib().mlp_unit_rates(*[ctypes.byref(x) for x in v]))
+    return tuple(x.value for x in v)

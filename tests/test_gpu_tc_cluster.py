@@ -139,3 +139,19 @@ def test_nonfinite_loss_is_reported():
         net.set(W)
         B.mlp_train_epochs(net.h, dev(I.bf16_bits(X).view(np.int16)), dev(y), n, 2, 0, None, None, stream())
         assert net.check() == B.MLP_ENONFINITE
+
+
+def test_wide_net_65536_row_subset_one_epoch():
+    """The wide workload's own schedule on its first 65,536 rows: 48-2048-1,
+    mini-batch 8192 (eight updates), against the oracle run of the same
+    schedule: loss within 2e-2, weight change within 4e-2, accuracy within one
+    point."""
+    n, H, mb = 65536, 2048, 8192
+    X, y, W = make(3600, n, H)
+    got, L = run(X, y, W, 1, lr32(), mb=mb)
+    q, lh, _ = oracle.train(X, y, Params(*W), lr32(), 1, minibatch=mb)
+    assert rel_err_elem(L, lh) <= BF16_GRAD_TOL
+    assert rel_err_norm(got - flat(W), q.flat() - flat(W)) <= 2 * BF16_GRAD_TOL
+    acc_gpu = (oracle.predict(X, unflat(got, H)) == y).mean()
+    acc_ref = (oracle.predict(X, q) == y).mean()
+    assert abs(acc_gpu - acc_ref) <= 0.01
