@@ -39,8 +39,6 @@ WORKLOAD = "33-64-1 sigmoid MLP, full-batch GD lr 0.1, 4096 rows x 33 features, 
 METRIC = "train sample-steps/s (fwd+bwd+update) vs plain FP32 path on 1 GB300; % roofline"
 FLOPS_PER_SAMPLE = 4 * D_IN * H_HID + 10 * H_HID   # forward 2DH+3H, backward 2DH+7H
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
-FUSED_SRCS = [os.path.join(ROOT, "paper_1908_07847_gb300", "csrc", f)
-              for f in ("fused_kernels.cu", "row_engine.cuh", "mlp_internal.cuh")]
 
 
 def parse():
@@ -49,6 +47,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--nets", type=int, default=0, help="c4 only: number of nets (default 1024; fewer for profiling)")
+    ap.add_argument("--epochs", type=int, default=0, help="c4 only: epochs per step (default 200)")
     ap.add_argument("--workload", default="c1", choices=["c1", "c2", "c3", "c4"],
                     help="c1: the 33-64-1 full-batch workload (default line); "
                          "c2: 4096 independent 33-H-1 nets, 500 epochs per step; "
@@ -170,21 +170,36 @@ def sfu_roofline(sigmoids_per_launch, launch_s, rates):
     return {"achieved_per_s": got, "peak_per_s": rates["tanh_per_s"], "frac": got / rates["tanh_per_s"],
             "peak_basis": "tanh.approx rate measured by mlp_unit_rates on this device"}
 
-def traffic_from_profile():
-    """DRAM bytes per launch of the fused kernel from the committed ncu summary,
-    if it was taken on the current kernel source; else None."""
-    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
-    try:
-        rec = json.load(open(path))
-        h = hashlib.sha256()
-        for f in FUSED_SRCS:
-            h.update(open(f, "rb").read())
-        src = h.hexdigest()[:16]
-        if rec.get("source_sha256_16") == src and rec.get("workload") == WORKLOAD:
-            return rec.get("dram_bytes_per_launch")
-    except Exception:
-        pass
+def traffic_record(kernel: str):
+    """The DRAM traffic record of `kernel` from the committed ncu summaries
+    (a `traffic-record:` line in profiles/*.md), if it was taken on the
+    current kernel sources; else None."""
+    import glob
+    csrc = os.path.join(ROOT, "paper_1908_07847_gb300", "csrc")
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        for line in open(path):
+            if not line.startswith("traffic-record:"):
+                continue
+            try:
+                rec = json.loads(line.split(":", 1)[1])
+            except ValueError:
+                continue
+            if rec.get("kernel") != kernel:
+                continue
+            h = hashlib.sha256()
+            try:
+                for f in rec["sources"]:
+                    h.update(open(os.path.join(csrc, f), "rb").read())
+            except (OSError, KeyError):
+                return None
+            return rec if h.hexdigest()[:16] == rec.get("source_sha256_16") else None
     return None
+
+
+def traffic_from_profile():
+    """DRAM bytes per launch of the fused kernel on the default workload."""
+    rec = traffic_record("k_fused_train")
+    return rec.get("dram_bytes_per_launch") if rec and rec.get("workload") == WORKLOAD else None
 
 
 def run_ours(args, rank, world, local):
@@ -563,9 +578,9 @@ def run_c3(args, rank, world, local):
     T_e = aggregate_max(t_e2e, world)
     units = C3_N * world
     launch_s = statistics.mean(times)
-    # algorithmic tensor-core work per row: X W1^T, d1^T [X | 1] (2 D H + 2 H
-    # each) and h^T d2 (2 H)
-    mma_flops = float(C3_N) * (4 * C3_D * C3_H + 6 * C3_H)
+    # algorithmic tensor-core work per row: X W1^T and d1^T X (2 D H each), gb1
+    # and gw2 (2 H each)
+    mma_flops = float(C3_N) * (4 * C3_D * C3_H + 4 * C3_H)
     peak = 1731.1   # MEASURED_PEAKS.json bf16_tflops_sustained
     out = {
         "metric": METRIC, "value": units * args.steps / T_f, "unit": "sample-steps/s", "n_gpus": world,
@@ -604,7 +619,9 @@ def run_c4(args, rank, world, local):
     stream = torch.cuda.current_stream().cuda_stream
     rates = unit_rates()
     seed = 4 + rank
-    _, ns = I.batched_shapes(seed, C4_NETS, (C4_H, C4_H), (4096, 16384))
+    n_nets = args.nets or C4_NETS
+    epochs = args.epochs or C4_EPOCHS
+    _, ns = I.batched_shapes(seed, n_nets, (C4_H, C4_H), (4096, 16384))
     offs = np.concatenate([[0], np.cumsum(ns)])
     total = int(offs[-1])
     Xall = torch.zeros((total, C4_D), dtype=torch.bfloat16, device=dev)
@@ -622,20 +639,20 @@ def run_c4(args, rank, world, local):
     yall = lab.to(torch.float32)
     P_per = (C4_D + 2) * C4_H + 1
     P0 = torch.from_numpy(np.concatenate([np.concatenate([a.ravel() for a in I.init_weights(
-        I.subseed(seed, 200 + t), 33, C4_H, C4_D)]) for t in range(C4_NETS)])).to(dev)
+        I.subseed(seed, 200 + t), 33, C4_H, C4_D)]) for t in range(n_nets)])).to(dev)
     Pw = P0.clone()
     descs = [B.mlp_net_desc(C4_H, int(ns[t]), Xall[int(offs[t]):].data_ptr(), yall[int(offs[t]):].data_ptr(),
-                            Pw[t * P_per:].data_ptr(), None) for t in range(C4_NETS)]
+                            Pw[t * P_per:].data_ptr(), None) for t in range(n_nets)]
     plan = B.mlp_batch_create(B.MLP_BF16, B.MLP_ACT_SIGMOID, C4_D, descs, LR, 1)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     g = torch.cuda.CUDAGraph()
     s2 = torch.cuda.Stream()
     s2.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(s2):
-        B.mlp_batch_run(plan, C4_EPOCHS, s2.cuda_stream)   # warm-up outside capture
+        B.mlp_batch_run(plan, epochs, s2.cuda_stream)   # warm-up outside capture
         s2.synchronize()
         with torch.cuda.graph(g, stream=s2):
-            B.mlp_batch_run(plan, C4_EPOCHS, s2.cuda_stream)
+            B.mlp_batch_run(plan, epochs, s2.cuda_stream)
     torch.cuda.current_stream().wait_stream(s2)
     for _ in range(max(args.warmup, 1)):
         Pw.copy_(P0)
@@ -655,22 +672,26 @@ def run_c4(args, rank, world, local):
     assert B.mlp_batch_check(plan, stream) == B.MLP_OK, B.mlp_last_error()
     B.mlp_batch_destroy(plan)
     T_f = aggregate_max(sum(times), world)
-    units = int(ns.sum()) * C4_EPOCHS * world
+    units = int(ns.sum()) * epochs * world
     # algorithmic tensor-core work per row-epoch: X W1^T and d1^T X (2 D H each),
     # gb1 and gw2 (2 H each)
-    mma_flops = float(ns.sum()) * C4_EPOCHS * (4 * C4_D * C4_H + 4 * C4_H)
+    mma_flops = float(ns.sum()) * epochs * (4 * C4_D * C4_H + 4 * C4_H)
     launch_s = statistics.mean(times)
     peak = 1731.1   # MEASURED_PEAKS.json bf16_tflops_sustained
+    # DRAM bytes of one launch, scaled by rows x epochs from the committed
+    # capture of a reduced case (X is read once per epoch at any size)
+    rec = traffic_record("k_tc_batched")
+    c4_traffic = rec["dram_bytes_per_row_epoch"] * float(ns.sum()) * epochs if rec else None
     out = {
         "metric": METRIC, "value": units * args.steps / T_f, "unit": "sample-steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": T_f / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-        "config": {"workload": C4_WORKLOAD, "nets": C4_NETS, "rows_total": int(ns.sum()), "epochs_per_step": C4_EPOCHS,
+        "config": {"workload": C4_WORKLOAD, "nets": n_nets, "rows_total": int(ns.sum()), "epochs_per_step": epochs,
                    "l2": "inputs (1 GB of bf16 X) larger than L2; L2 also flushed between timed steps"},
         "roofline": {"bound": "tensor", "achieved": mma_flops / launch_s / 1e12, "peak": peak, "unit": "TFLOP/s",
-                     "frac": mma_flops / launch_s / 1e12 / peak, "traffic": None, "kernel": "k_tc_batched",
+                     "frac": mma_flops / launch_s / 1e12 / peak, "traffic": c4_traffic, "kernel": "k_tc_batched",
                      "peak_basis": "bf16_tflops_sustained of measured", "flops_per_launch": mma_flops,
-                     "sfu": sfu_roofline(float(ns.sum()) * C4_EPOCHS * (C4_H + 1), launch_s, rates)},
+                     "sfu": sfu_roofline(float(ns.sum()) * epochs * (C4_H + 1), launch_s, rates)},
         "gpu_launches": args.steps, "clocks": clk.summary(),
     }
     if rank == 0:

@@ -127,9 +127,18 @@ mlp_status mlp_step_plain(mlp_t net, const void *X, const void *y, int64_t n,
  * loss_hist [epochs] (device, may be NULL) receives (C/2) sum_i (o_i - y_i)^2
  * with o_i taken when row i was visited (C = 1/n or 1), accumulated in FP64;
  * gnorm_hist [epochs] (device, may be NULL) the FP64 2-norm of the last
- * update's gradient.  Small networks run as one fused cooperative kernel per
- * call (forward, backward, cross-block reduction and update per step); larger
- * ones fall back to the plain path per step. */
+ * update's gradient.  Paths, by precision and shape:
+ *   MLP_FP32, D <= 64, H <= 128: one fused cooperative kernel per call
+ *     (forward, backward, cross-block reduction and update per step);
+ *   MLP_BF16, sigmoid, D % 8 == 0, 8 <= D <= 48, H a multiple of 256 up to
+ *     2048, gnorm_hist NULL: one tensor-core (tcgen05) kernel per call, blocks
+ *     in clusters of H/256 that share z2 through distributed shared memory,
+ *     bf16 operands (W1, h and the hidden deltas rounded to bf16, FP32
+ *     accumulation and FP32 master weights); X must be 16-byte aligned;
+ *   everything else: the plain path, one step at a time (FP32 arithmetic on
+ *     bf16 inputs for MLP_BF16).
+ * The tensor-core kernel records MLP_ECUDA through mlp_check if it ever finds
+ * itself launched without its cluster shape. */
 mlp_status mlp_train_epochs(mlp_t net, const void *X, const void *y, int64_t n,
                             int32_t epochs, int64_t minibatch, double *loss_hist,
                             double *gnorm_hist, void *stream);
@@ -188,8 +197,11 @@ mlp_status mlp_set_rows_per_block(mlp_t net, int32_t rows);
  * X (n x D row-major, float), y (n floats), params (the net's packed weights
  * [W1 (H x D), b1, w2, b2], float, trained in place) and loss_hist (epochs
  * doubles, may be NULL; receives the loss before each epoch's update).
- * Limits of this build: MLP_FP32, D <= 64, H <= 128; n is unbounded (rows
- * beyond 256 are streamed from device memory each epoch).
+ * Limits of this build: MLP_FP32 (FP32 X): D <= 64, H <= 128; n is unbounded
+ * (rows beyond 256 are streamed from device memory each epoch).  MLP_BF16
+ * (bf16 X, 16-byte aligned, padding columns zero; FP32 master weights,
+ * tcgen05 tensor cores, one block per net): sigmoid only, D % 8 == 0,
+ * 8 <= D <= 56, H = 128 or 256.
  */
 typedef struct {
     int32_t H;
