@@ -77,6 +77,8 @@ def _bind(lib):
     lib.orc_train.argtypes = [i, i, l, p, p, p, p, p, p, i, i, d, i, l, p, p]
     lib.orc_predict.restype = None
     lib.orc_predict.argtypes = [i, i, l, p, p, p, p, d, i, p]
+    lib.orc_zscore.restype = None
+    lib.orc_zscore.argtypes = [l, i, l, p, p, p, p]
     lib.orc_batch_train.restype = None
     lib.orc_batch_train.argtypes = [i, p, p, p, p, p, p, p, p, p, i, i, d, i, l, p, i]
     return lib
@@ -274,3 +276,18 @@ def batch_train(nets, lr: float, epochs: int, minibatch: int = 0,
 
 if __name__ == "__main__":  # pragma: no cover - manual build entry
     print(build(force="--force" in sys.argv))
+
+
+def zscore(X, n_fit=None):
+    """Column z-score with the statistics of the first n_fit rows (Sec. 2.2's
+    normalisation, read as training-set mean and population deviation);
+    returns (Y, mean, sdev)."""
+    lib = _load()
+    X = _f64(X)
+    n, D = X.shape
+    n_fit = n if n_fit is None else int(n_fit)
+    mean = np.zeros(D)
+    sdev = np.zeros(D)
+    Y = np.zeros((n, D))
+    lib.orc_zscore(n, D, n_fit, _ptr(X), _ptr(mean), _ptr(sdev), _ptr(Y))
+    return Y, mean, sdev

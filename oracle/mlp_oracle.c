@@ -282,3 +282,29 @@ void orc_batch_train(int n_nets, const int *Ds, const int *Hs, const long *ns,
                   loss_all ? loss_all + (long)t * epochs : NULL, NULL);
     }
 }
+
+/*
+ * Sec. 2.2: the data are normalised before training (the paper does not say
+ * how).  Reading: z-score per column with statistics of the training rows
+ * only (the first n_fit rows): mean_j = (1/n_fit) sum_i X[i][j], the
+ * population deviation s_j = sqrt((1/n_fit) sum_i (X[i][j] - mean_j)^2), and
+ * Y[i][j] = (X[i][j] - mean_j) / s_j for every row i < n, or 0 where s_j = 0
+ * (a constant column carries no information).  Sums in increasing row order.
+ */
+void orc_zscore(long n, int D, long n_fit, const double *X, double *mean, double *sdev, double *Y)
+{
+    for (int j = 0; j < D; ++j) {
+        double s = 0.0;
+        for (long i = 0; i < n_fit; ++i) s += X[i * D + j];
+        const double m = s / (double)n_fit;
+        double q = 0.0;
+        for (long i = 0; i < n_fit; ++i) {
+            const double d = X[i * D + j] - m;
+            q += d * d;
+        }
+        const double sd = sqrt(q / (double)n_fit);
+        mean[j] = m;
+        sdev[j] = sd;
+        for (long i = 0; i < n; ++i) Y[i * D + j] = sd > 0.0 ? (X[i * D + j] - m) / sd : 0.0;
+    }
+}

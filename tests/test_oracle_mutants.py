@@ -38,6 +38,10 @@ MUTANTS = {
     "loss_hist_half_dropped": ("loss_hist[e] = 0.5 * sse", "loss_hist[e] = sse"),
     "minibatch_loss_last_batch_only": ("sse += orc_mse_gradients(", "sse = orc_mse_gradients("),
     "gnorm_missing_b2": ("    s += gb2 * gb2;\n", "\n"),
+    "zscore_sample_deviation": ("sqrt(q / (double)n_fit)", "sqrt(q / (double)(n_fit - 1))"),
+    "zscore_stats_over_all_rows": ("for (long i = 0; i < n_fit; ++i) s += X[i * D + j];",
+                                   "for (long i = 0; i < n; ++i) s += X[i * D + j];"),
+    "zscore_not_centred": ("(X[i * D + j] - m) / sd", "X[i * D + j] / sd"),
 }
 
 PINS = [
@@ -55,6 +59,8 @@ PINS = [
     P.test_minibatch_is_sequence_of_full_batch_steps,
     P.test_predict_threshold_and_tie,
     P.test_empty_input,
+    P.test_zscore_statistics_match_numpy_population_moments,
+    P.test_zscore_affine_invariance_constant_column_and_test_rows,
 ]
 
 

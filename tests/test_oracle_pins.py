@@ -425,3 +425,50 @@ def test_split_rule_reproduces_paper_accuracies():
         assert any(round(100.0 * k / ntr, 2) == tr for k in range(ntr + 1)), name
         assert any(round(100.0 * k / nte, 2) == te for k in range(nte + 1)), name
     assert (I.split_count(61), I.split_count(59)) == (46, 44)
+
+
+# ------------------------------------------------- z-score normalisation ----
+
+def _zdata(seed=11, n=400, D=7):
+    rng = np.random.default_rng(seed)
+    X = rng.normal(size=(n, D)) * rng.uniform(0.5, 4.0, D) + rng.uniform(-10, 10, D)
+    X[:, 3] = 2.5   # a constant column
+    return X
+
+
+def test_zscore_statistics_match_numpy_population_moments():
+    """Mean and population deviation (ddof 0) of the fit rows, as numpy
+    computes them; the test rows use the fit rows' statistics."""
+    X = _zdata()
+    n_fit = 300
+    Y, m, s = oracle.zscore(X, n_fit)
+    np.testing.assert_allclose(m, X[:n_fit].mean(axis=0), rtol=1e-13, atol=1e-13)
+    np.testing.assert_allclose(s, X[:n_fit].std(axis=0, ddof=0), rtol=1e-12, atol=1e-15)
+    ok = s > 0
+    np.testing.assert_allclose(Y[:, ok], (X[:, ok] - m[ok]) / s[ok], rtol=1e-12, atol=1e-12)
+
+
+def test_zscore_fit_rows_have_zero_mean_unit_deviation():
+    X = _zdata(12)
+    Y, m, s = oracle.zscore(X, 250)
+    ok = s > 0
+    np.testing.assert_allclose(Y[:250, ok].mean(axis=0), 0.0, atol=1e-12)
+    np.testing.assert_allclose(np.sqrt((Y[:250, ok] ** 2).mean(axis=0)), 1.0, rtol=1e-12)
+
+
+def test_zscore_affine_invariance_constant_column_and_test_rows():
+    """Scaling a column by a > 0 and shifting it leaves the output unchanged; a
+    constant column maps to 0; changing test rows changes no statistic."""
+    X = _zdata(13)
+    Y, m, s = oracle.zscore(X, 200)
+    X2 = X * 3.0 + 7.0
+    Y2, _, _ = oracle.zscore(X2, 200)
+    np.testing.assert_allclose(Y2, Y, rtol=1e-9, atol=1e-9)
+    assert s[3] == 0.0 and np.all(Y[:, 3] == 0.0)
+    X3 = X.copy()
+    X3[200:] = 1e6
+    _, m3, s3 = oracle.zscore(X3, 200)
+    np.testing.assert_array_equal(m3, m)
+    np.testing.assert_array_equal(s3, s)
+    Y1, m1, s1 = oracle.zscore(X[:5], 1)     # one fit row: no spread anywhere
+    assert np.all(s1 == 0.0) and np.all(Y1 == 0.0)
