@@ -269,6 +269,29 @@ mlp_status mlp_train_fused_noalloc(int32_t act, int32_t D, int32_t H, int64_t n,
                                    int64_t minibatch, double *loss_hist,
                                    int32_t *status_out, void *stream);
 
+/* Z-score normalisation of the feature table (Sec. 2.2 normalises the data
+ * before training; the reading: per-column mean and population standard
+ * deviation of the first n_fit rows, the training rows, applied to all n rows;
+ * a column with zero deviation maps to 0), fused with the conversion to the
+ * layout the training calls read.
+ *   X      n x D float, row-major (device); must not overlap Y.
+ *   Y      n x D_out (D_out >= D) of out_prec: MLP_FP32 (float) or MLP_BF16
+ *          (bfloat16 bits, round to nearest even); columns D..D_out-1 are 0,
+ *          so a bf16 output with D_out = 48 is the padded input of the
+ *          tensor-core paths.
+ *   mean, sdev  D doubles each (device): the statistics used.
+ *   workspace   device scratch of at least mlp_zscore_workspace_bytes(D).
+ * The statistics are FP64 sums in a fixed order (bitwise reproducible); the
+ * normalisation is FP32, ((x - m_hi) - m_lo) * (1/s) with the mean split
+ * into two floats.  n = 0 does nothing.  MLP_EINVAL: a NULL pointer, D < 1,
+ * D_out < D, n_fit outside 1..n, a bad precision or a short workspace;
+ * MLP_EUNSUPPORTED: D > 4096.  Asynchronous on `stream`. */
+mlp_status mlp_zscore_workspace_bytes(int32_t D, uint64_t *bytes);
+mlp_status mlp_zscore(const float *X, int64_t n, int32_t D, int64_t n_fit,
+                      int32_t out_prec, int32_t D_out, void *Y, double *mean,
+                      double *sdev, void *workspace, uint64_t workspace_bytes,
+                      void *stream);
+
 /* Diagnostic, not part of the method: measured rates of the FP32 FMA pipe and
  * of the special-function unit for tanh.approx.f32 and ex2.approx.f32, in
  * instructions per second over the whole current device (CUDA-event timed

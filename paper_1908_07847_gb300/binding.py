@@ -26,7 +26,7 @@ EXPORTS = [
     "mlp_train_host", "mlp_predict", "mlp_check", "mlp_workspace_bytes", "mlp_forward_w",
     "mlp_backward_w", "mlp_debug_skip_block", "mlp_set_rows_per_block", "mlp_batch_train",
     "mlp_batch_create", "mlp_batch_run", "mlp_batch_check", "mlp_batch_destroy", "mlp_train_fused_noalloc",
-    "mlp_unit_rates", "mlp_last_error", "mlp_version",
+    "mlp_zscore_workspace_bytes", "mlp_zscore", "mlp_unit_rates", "mlp_last_error", "mlp_version",
 ]
 
 
@@ -93,6 +93,8 @@ def lib():
             "mlp_last_error": (ctypes.c_char_p, []),
             "mlp_version": (ctypes.c_char_p, []),
             "mlp_unit_rates": (S, [ctypes.POINTER(ctypes.c_double)] * 3),
+            "mlp_zscore_workspace_bytes": (S, [I32, ctypes.POINTER(U64)]),
+            "mlp_zscore": (S, [V, I64, I32, I64, I32, I32, V, V, V, V, U64, V]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -255,3 +257,14 @@ def mlp_unit_rates():
     v = [ctypes.c_double() for _ in range(3)]
     _ck(lib().mlp_unit_rates(*[ctypes.byref(x) for x in v]))
     return tuple(x.value for x in v)
+
+
+def mlp_zscore_workspace_bytes(D):
+    b = ctypes.c_uint64()
+    _ck(lib().mlp_zscore_workspace_bytes(D, ctypes.byref(b)))
+    return b.value
+
+
+def mlp_zscore(X, n, D, n_fit, out_prec, D_out, Y, mean, sdev, workspace, workspace_bytes, stream=0):
+    return _ck(lib().mlp_zscore(_p(X), n, D, n_fit, out_prec, D_out, _p(Y), _p(mean), _p(sdev), _p(workspace),
+                                workspace_bytes, stream))

@@ -150,6 +150,8 @@ mlp_status check_handle(mlp_t h) {
 mlp_status noalloc_fail(mlp_status s, const char *msg) { return fail(s, "%s", msg); }
 
 namespace mlp {
+mlp_status set_error(mlp_status s, const char *msg) { return fail(s, "%s", msg); }
+
 int device_sm_count() {
     int dev = 0, n = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 1;

@@ -272,4 +272,7 @@ cudaError_t tc_cluster_train(const void *X, const float *y, float *params, int D
 
 int device_sm_count();
 
+// Records msg as the calling thread's last error (mlp_last_error) and returns s.
+mlp_status set_error(mlp_status s, const char *msg);
+
 }  // namespace mlp

@@ -6,7 +6,7 @@
 // whole device, timed with CUDA events.
 #include <cuda_runtime.h>
 
-#include "mlp_gb300.h"
+#include "mlp_internal.cuh"
 
 namespace {
 
@@ -53,17 +53,20 @@ cudaError_t rate(unsigned *buf, int blocks, int threads, double *per_s) {
 }  // namespace
 
 extern "C" mlp_status mlp_unit_rates(double *ffma_per_s, double *tanh_per_s, double *ex2_per_s) {
-    if (!ffma_per_s || !tanh_per_s || !ex2_per_s) return MLP_EINVAL;
+    if (!ffma_per_s || !tanh_per_s || !ex2_per_s) return mlp::set_error(MLP_EINVAL, "mlp_unit_rates: null pointer");
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-        return MLP_ECUDA;
+        return mlp::set_error(MLP_ECUDA, "mlp_unit_rates: no device");
     const int blocks = 4 * sms, threads = 512;
     unsigned *buf = nullptr;
-    if (cudaMalloc((void **)&buf, sizeof(unsigned) * blocks * threads) != cudaSuccess) return MLP_ENOMEM;
+    if (cudaMalloc((void **)&buf, sizeof(unsigned) * blocks * threads) != cudaSuccess) {
+        cudaGetLastError();
+        return mlp::set_error(MLP_ENOMEM, "mlp_unit_rates: cannot allocate");
+    }
     cudaError_t e = rate<0>(buf, blocks, threads, ffma_per_s);
     if (e == cudaSuccess) e = rate<1>(buf, blocks, threads, tanh_per_s);
     if (e == cudaSuccess) e = rate<2>(buf, blocks, threads, ex2_per_s);
     cudaFree(buf);
-    return e == cudaSuccess ? MLP_OK : MLP_ECUDA;
+    return e == cudaSuccess ? MLP_OK : mlp::set_error(MLP_ECUDA, cudaGetErrorString(e));
 }
