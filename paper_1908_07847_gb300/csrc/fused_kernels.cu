@@ -105,8 +105,6 @@ __global__ void __launch_bounds__(FNT, 2) k_fused_train(FArgs a) {
     const float gup = __int_as_float((127 + a.gshift) << 23);      // 2^gshift
     const double Cl = a.loss_mean ? (a.n > 0 ? 1.0 / (double)a.n : 0.0) : 1.0;
 
-    for (int i = tid; i < xcap * DP; i += FNT) Xs[i] = 0.f;
-    __syncthreads();
     {
         // Initial weights: 16-byte copies through L2, then the tail.
         const int P4 = P & ~3;
@@ -125,6 +123,10 @@ __global__ void __launch_bounds__(FNT, 2) k_fused_train(FArgs a) {
         const int64_t r0 = (mbs * g) / G, r1 = (mbs * (g + 1)) / G;
         if (r1 > r0) stage(r0, (int)(r1 - r0));
     }
+    // Only the padding columns D..DP-1 of the row buffer are read without
+    // being copied; zero them while the copies are in flight (disjoint words).
+    if (DP > D)
+        for (int i = tid; i < xcap * (DP - D); i += FNT) Xs[(i / (DP - D)) * DP + D + i % (DP - D)] = 0.f;
     cp_async_wait_all();
     __syncthreads();
 
@@ -182,15 +184,15 @@ __global__ void __launch_bounds__(FNT, 2) k_fused_train(FArgs a) {
             // ---- every block applies the summed gradient to its own copy
             const bool want_gn = g == 0 && a.gnorm_hist && epoch_end;
             double gn = 0.0;
-            for (int base = 0; base < P; base += 8 * FNT) {
-                long long v[8];  // eight loads in flight per thread
+            for (int base = 0; base < P; base += 12 * FNT) {
+                long long v[12];  // twelve loads in flight per thread: one round trip up to P = 3072
 #pragma unroll
-                for (int r = 0; r < 8; ++r) {
+                for (int r = 0; r < 12; ++r) {
                     const int p = base + r * FNT + tid;
                     v[r] = (p < P) ? __ldcg(acc + p) : 0ll;
                 }
 #pragma unroll
-                for (int r = 0; r < 8; ++r) {
+                for (int r = 0; r < 12; ++r) {
                     const int p = base + r * FNT + tid;
                     if (p < P) {
                         const float gsum = (float)v[r] * gscale;
