@@ -296,12 +296,12 @@ __global__ void __launch_bounds__(NT, 1) k_tc_cluster(const __grid_constant__ CU
                     const bool valid = trow < m;
                     const float yv = valid ? a.y[b0 + trow] : 0.f;
                     if (!mbar_wait(BAR_Z1F, z1f_use++ & 1, abort)) { eok = false; break; }
-                    if (!mbar_wait(BAR_HE, (he_use++ & 1) ^ 1, abort)) { eok = false; break; }
                     tc_fence_after();
                     // pass 1: h = sigmoid(z1) in bf16 pairs (written as h^T), this
                     // block's share of z2 = h w2 with FP32 accumulation
                     uint32_t hp[64];
                     float zp[4] = {0.f, 0.f, 0.f, 0.f};
+                    bool heok = true;
 #pragma unroll
                     for (int ch = 0; ch < 4; ++ch) {
                         const int c0 = cb + 32 * ch;
@@ -317,12 +317,24 @@ __global__ void __launch_bounds__(NT, 1) k_tc_cluster(const __grid_constant__ CU
                             zp[2] = dot2_bf16(hp[16 * ch + u + 2], w.z, zp[2]);
                             zp[3] = dot2_bf16(hp[16 * ch + u + 3], w.w, zp[3]);
                         }
+                        // h^T from the second chunk on: the previous tile's gw2 MMA
+                        // is done with h^T and d2 by then (waited for here, halfway)
+                        if (ch == 1) {
+                            if (!mbar_wait(BAR_HE, (he_use++ & 1) ^ 1, abort)) { heok = false; break; }
 #pragma unroll
-                        for (int v = 0; v < 4; ++v)
-                            *(uint4 *)(sm + SM_HT + mnmajor_chunk(c0 + 8 * v, r)) =
-                                make_uint4(hp[16 * ch + 4 * v], hp[16 * ch + 4 * v + 1], hp[16 * ch + 4 * v + 2],
-                                           hp[16 * ch + 4 * v + 3]);
+                            for (int v = 0; v < 4; ++v)
+                                *(uint4 *)(sm + SM_HT + mnmajor_chunk(cb + 8 * v, r)) =
+                                    make_uint4(hp[4 * v], hp[4 * v + 1], hp[4 * v + 2], hp[4 * v + 3]);
+                        }
+                        if (ch >= 1) {
+#pragma unroll
+                            for (int v = 0; v < 4; ++v)
+                                *(uint4 *)(sm + SM_HT + mnmajor_chunk(c0 + 8 * v, r)) =
+                                    make_uint4(hp[16 * ch + 4 * v], hp[16 * ch + 4 * v + 1], hp[16 * ch + 4 * v + 2],
+                                               hp[16 * ch + 4 * v + 3]);
+                        }
                     }
+                    if (!heok) { eok = false; break; }
                     tc_fence_before();
                     mbar_arrive(BAR_Z1E);
                     // this block's share of z2 (both halves), pushed into every

@@ -286,13 +286,12 @@ __global__ void __launch_bounds__(NT, 1) k_tc_batched(TcArgs a) {
                     const float yv = y_next;
                     if (row + TR < n) y_next = nd.y[row + TR];
                     if (!mbar_wait(BAR_Z1F, z1f_use++ & 1, abort)) { ok = false; break; }
-                    // the previous tile's gw2 MMA must be done with h^T and d2
-                    if (!mbar_wait(BAR_HE, (he_use++ & 1) ^ 1, abort)) { ok = false; break; }
                     tc_fence_after();
                     // pass 1: h = sigmoid(z1) in bf16 pairs -> h^T, this half's
                     // share of z2 = h w2 in FP32
                     uint32_t hp[64];
                     float zp[4] = {0.f, 0.f, 0.f, 0.f};
+                    bool heok = true;
 #pragma unroll
                     for (int ch = 0; ch < 4; ++ch) {
                         if (ch >= nch) break;
@@ -309,12 +308,24 @@ __global__ void __launch_bounds__(NT, 1) k_tc_batched(TcArgs a) {
                             zp[2] = dot2_bf16(hp[16 * ch + u + 2], w.z, zp[2]);
                             zp[3] = dot2_bf16(hp[16 * ch + u + 3], w.w, zp[3]);
                         }
+                        // h^T from the second chunk on: the previous tile's gw2 MMA
+                        // is done with h^T and d2 by then (waited for here, halfway)
+                        if (ch == 1) {
+                            if (!mbar_wait(BAR_HE, (he_use++ & 1) ^ 1, abort)) { heok = false; break; }
 #pragma unroll
-                        for (int v = 0; v < 4; ++v)
-                            *(uint4 *)(sm + SM_HT + mnmajor_chunk(c0 + 8 * v, r)) =
-                                make_uint4(hp[16 * ch + 4 * v], hp[16 * ch + 4 * v + 1], hp[16 * ch + 4 * v + 2],
-                                           hp[16 * ch + 4 * v + 3]);
+                            for (int v = 0; v < 4; ++v)
+                                *(uint4 *)(sm + SM_HT + mnmajor_chunk(cb + 8 * v, r)) =
+                                    make_uint4(hp[4 * v], hp[4 * v + 1], hp[4 * v + 2], hp[4 * v + 3]);
+                        }
+                        if (ch >= 1) {
+#pragma unroll
+                            for (int v = 0; v < 4; ++v)
+                                *(uint4 *)(sm + SM_HT + mnmajor_chunk(c0 + 8 * v, r)) =
+                                    make_uint4(hp[16 * ch + 4 * v], hp[16 * ch + 4 * v + 1], hp[16 * ch + 4 * v + 2],
+                                               hp[16 * ch + 4 * v + 3]);
+                        }
                     }
+                    if (!heok) { ok = false; break; }
                     tc_fence_before();
                     mbar_arrive(BAR_Z1E);  // Z1 in tensor memory may be overwritten
                     // the two halves' shares of z2 meet in shared memory; while the
