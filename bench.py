@@ -162,6 +162,36 @@ def unit_rates():
     return {"ffma_tflops": 2 * ffma / 1e12, "tanh_per_s": tanh, "ex2_per_s": ex2}
 
 
+def host_cpu():
+    """Host core count and CPU model (lscpu), for the oracle baselines."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"cores_available": os.cpu_count(), "cpu_model": model}
+
+
+def plain_rate(B, h, X, y, rows, steps, stream):
+    """sample-steps/s of the plain path (separate forward, output, gradient,
+    reduction and update kernels, mlp_step_plain) on `rows` rows, CUDA events."""
+    import torch
+    loss = torch.zeros(1, dtype=torch.float64, device=X.device)
+    for _ in range(3):
+        B.mlp_step_plain(h, X, y, rows, loss, stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        B.mlp_step_plain(h, X, y, rows, loss, stream)
+    e1.record()
+    torch.cuda.synchronize()
+    return rows * steps / (e0.elapsed_time(e1) * 1e-3)
+
+
 def sfu_roofline(sigmoids_per_launch, launch_s, rates):
     """Sigmoids per second against the measured tanh rate of the SFU (the bf16
     paths evaluate every sigmoid as one tanh, two per bf16x2 instruction at the
@@ -332,7 +362,8 @@ def oracle_epoch_rate(budget_s: float, rows: int):
 def cpu_baseline():
     rate, epochs, rows = oracle_epoch_rate(10.0, N_ROWS)
     return {"value": rate, "unit": "sample-steps/s", "cores": 1, "kind": "oracle",
-            "sample": "%d full-batch epochs over all %d rows (serial FP64 C oracle, one thread)" % (epochs, rows)}
+            "sample": "%d full-batch epochs over all %d rows (serial FP64 C oracle, one thread)" % (epochs, rows),
+            **host_cpu()}
 
 
 def run_reference(args, rank, world):
@@ -445,6 +476,13 @@ def run_c2(args, rank, world, local):
             times.append(e0.elapsed_time(e1) * 1e-3)
     assert B.mlp_batch_check(plan, stream) == B.MLP_OK, B.mlp_last_error()
     B.mlp_batch_destroy(plan)
+    # the plain path, one net at a time (a mid-size net of the sample), for the
+    # speedup of the one-launch many-nets kernel over it
+    t_mid = int(np.argsort(ns * Hs)[C2_NETS // 2])
+    hp = B.mlp_create(D_IN, int(Hs[t_mid]), LR, 1, B.MLP_FP32, B.MLP_ACT_SIGMOID)
+    B.mlp_set_weights(hp, *nets[t_mid][1])
+    plain = plain_rate(B, hp, Xall[int(offs_x[t_mid]):], yall[int(offs_x[t_mid]):], int(ns[t_mid]), 200, stream)
+    B.mlp_destroy(hp)
     T_f = aggregate_max(sum(times), world)
     units = int(ns.sum()) * C2_EPOCHS * world
     flops = float(np.sum(ns * (4 * D_IN * Hs + 10 * Hs))) * C2_EPOCHS
@@ -459,10 +497,56 @@ def run_c2(args, rank, world, local):
         "roofline": {"bound": "alu", "achieved": flops / launch_s / 1e12, "peak": peak, "unit": "TFLOP/s",
                      "frac": flops / launch_s / 1e12 / peak, "traffic": None, "kernel": "k_batched_train<36,sigmoid>",
                      "flops_per_launch": flops},
+        "plain_fp32": {"value": plain, "unit": "sample-steps/s",
+                       "path": "mlp_step_plain on one mid-size net of the workload (the plain path takes one net "
+                               "at a time)", "speedup_of_batched": units * steps / T_f / plain},
         "gpu_launches": steps, "clocks": clk.summary(),
     }
     if rank == 0:
+        out["cpu_baseline"], out["parity"] = c2_oracle_leg(Hs, ns, nets)
         print(json.dumps(out), flush=True)
+
+
+def c2_oracle_leg(Hs, ns, nets, sample=16):
+    """The FP64 oracle on `sample` nets of the workload for all 500 epochs
+    (OpenMP over nets on every host core), timed; the library's batch plan on
+    the same nets and oracle-made labels, compared after the 500 epochs."""
+    import torch
+    import oracle
+    from paper_1908_07847_gb300 import binding as B
+    from paper_1908_07847_gb300 import inputs as I
+    T = oracle.Params(*I.teacher_weights(D=D_IN))
+    sel = list(range(sample))
+    onets = []
+    for t in sel:
+        X = nets[t][0].astype(np.float64)
+        onets.append((X, oracle.predict(X, T).astype(np.float64), oracle.Params(*nets[t][1])))
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    out, _ = oracle.batch_train(onets, float(np.float32(LR)), C2_EPOCHS, threads=threads)
+    dt = time.perf_counter() - t0
+    dev = torch.device("cuda")
+    keep, descs, params = [], [], []
+    for (X, y, p) in onets:
+        Xd = torch.from_numpy(X.astype(np.float32)).to(dev)
+        yd = torch.from_numpy(y.astype(np.float32)).to(dev)
+        P = torch.from_numpy(p.flat().astype(np.float32)).to(dev)
+        keep += [Xd, yd]
+        params.append(P)
+        descs.append(B.mlp_net_desc(p.H, X.shape[0], Xd.data_ptr(), yd.data_ptr(), P.data_ptr(), None))
+    plan = B.mlp_batch_create(B.MLP_FP32, B.MLP_ACT_SIGMOID, D_IN, descs, LR, 1)
+    B.mlp_batch_run(plan, C2_EPOCHS, torch.cuda.current_stream().cuda_stream)
+    assert B.mlp_batch_check(plan, torch.cuda.current_stream().cuda_stream) == B.MLP_OK, B.mlp_last_error()
+    B.mlp_batch_destroy(plan)
+    err = max(float(np.max(np.abs(P.cpu().numpy() - q.flat())) / np.max(np.abs(q.flat())))
+              for P, q in zip(params, out))
+    rows = int(sum(ns[t] for t in sel))
+    cpu = {"value": rows * C2_EPOCHS / dt, "unit": "sample-steps/s", "cores": threads, "kind": "oracle",
+           "sample": "%d of the nets, all %d epochs (FP64 C oracle, OpenMP over nets)" % (sample, C2_EPOCHS),
+           **host_cpu()}
+    parity = {"nets": sample, "epochs": C2_EPOCHS, "measure": "max over nets of max |w - w*| / max |w*|",
+              "value": err}
+    return cpu, parity
 
 
 # --------------------------------- one wide bf16 tensor-core net (c3) ------
@@ -524,7 +608,8 @@ def c3_oracle_leg(X, W):
     dg, dr = flat(W1, b1, w2, b2) - w0, q.flat() - w0
     err = float(np.max(np.abs(dg - dr)) / np.max(np.abs(dr)))
     cpu = {"value": C3_SUB / dt, "unit": "sample-steps/s", "cores": 1, "kind": "oracle",
-           "sample": "one mini-batch step over the first %d rows (serial FP64 C oracle, one thread)" % C3_SUB}
+           "sample": "one mini-batch step over the first %d rows (serial FP64 C oracle, one thread)" % C3_SUB,
+           **host_cpu()}
     parity = {"rows": C3_SUB, "steps": 1, "measure": "max |dw - dw*| / max |dw*| of the weight update",
               "value": err, "tolerance": 2e-2}
     return cpu, parity
@@ -572,6 +657,9 @@ def run_c3(args, rank, world, local):
         B.mlp_train_host(h, Xh, yh, C3_N, 1, C3_MB, lh, stream)
     torch.cuda.synchronize()
     t_e2e = time.perf_counter() - t0
+    # the plain path (separate kernels per step, FP32 arithmetic on the bf16
+    # rows) on mini-batches of 8192 rows of the same net
+    plain = plain_rate(B, h, X, y, C3_MB, 20, stream)
     B.mlp_destroy(h)
     barrier(world)
     T_f = aggregate_max(sum(times), world)
@@ -592,6 +680,9 @@ def run_c3(args, rank, world, local):
         "e2e": {"value": units * e2e_steps / T_e, "unit": "sample-steps/s",
                 "h2d_bytes_per_step": C3_N * C3_D * 2 + C3_N * 4, "d2h_bytes_per_step": 8,
                 "call": "mlp_train_host (pinned host X, y in; loss out)"},
+        "plain_fp32": {"value": plain, "unit": "sample-steps/s",
+                       "path": "mlp_step_plain on 8192-row mini-batches (FP32 arithmetic on bf16 rows)",
+                       "speedup_of_tensor_core": units * args.steps / T_f / plain},
         "roofline": {"bound": "tensor", "achieved": mma_flops / launch_s / 1e12, "peak": peak, "unit": "TFLOP/s",
                      "frac": mma_flops / launch_s / 1e12 / peak, "traffic": None, "kernel": "k_tc_cluster",
                      "peak_basis": "bf16_tflops_sustained of measured", "flops_per_launch": mma_flops,
@@ -671,6 +762,13 @@ def run_c4(args, rank, world, local):
             times.append(e0.elapsed_time(e1) * 1e-3)
     assert B.mlp_batch_check(plan, stream) == B.MLP_OK, B.mlp_last_error()
     B.mlp_batch_destroy(plan)
+    # the plain path on net 0 (separate kernels per step, FP32 arithmetic on its
+    # bf16 rows), for the speedup of the one-launch tensor-core kernel over it
+    hp = B.mlp_create(C4_D, C4_H, LR, 1, B.MLP_BF16, B.MLP_ACT_SIGMOID)
+    B.mlp_set_weights(hp, *[np.ascontiguousarray(np.asarray(a_, np.float32)) for a_ in
+                            I.init_weights(I.subseed(seed, 200), 33, C4_H, C4_D)])
+    plain = plain_rate(B, hp, Xall, yall, int(ns[0]), 50, stream)
+    B.mlp_destroy(hp)
     T_f = aggregate_max(sum(times), world)
     units = int(ns.sum()) * epochs * world
     # algorithmic tensor-core work per row-epoch: X W1^T and d1^T X (2 D H each),
@@ -692,10 +790,55 @@ def run_c4(args, rank, world, local):
                      "frac": mma_flops / launch_s / 1e12 / peak, "traffic": c4_traffic, "kernel": "k_tc_batched",
                      "peak_basis": "bf16_tflops_sustained of measured", "flops_per_launch": mma_flops,
                      "sfu": sfu_roofline(float(ns.sum()) * epochs * (C4_H + 1), launch_s, rates)},
+        "plain_fp32": {"value": plain, "unit": "sample-steps/s",
+                       "path": "mlp_step_plain on one net of the workload (FP32 arithmetic on bf16 rows)",
+                       "speedup_of_tensor_core": units * args.steps / T_f / plain},
         "gpu_launches": args.steps, "clocks": clk.summary(),
     }
     if rank == 0:
+        out["cpu_baseline"], out["parity"] = c4_oracle_leg(seed, ns)
         print(json.dumps(out), flush=True)
+
+
+def c4_oracle_leg(seed, ns, sample=2, epochs=3):
+    """The FP64 oracle on the first `sample` nets of the workload for `epochs`
+    epochs (their bf16 rows regenerated on the host, labels by the oracle's
+    teacher predict), timed; the library's bf16 batch plan on the same nets and
+    labels, compared by the weight change."""
+    import torch
+    import oracle
+    from paper_1908_07847_gb300 import binding as B
+    from paper_1908_07847_gb300 import inputs as I
+    rows = int(sum(ns[:sample]))
+    Xh = I.bf16_round(I.features(I.subseed(seed, 10_000), rows, 33, C4_D)).astype(np.float64)
+    T = oracle.Params(*I.teacher_weights(D=33, Dpad=C4_D))
+    yh = oracle.predict(Xh, T).astype(np.float64)
+    offs = np.concatenate([[0], np.cumsum(ns[:sample])])
+    onets = [(Xh[offs[t]:offs[t + 1]], yh[offs[t]:offs[t + 1]],
+              oracle.Params(*I.init_weights(I.subseed(seed, 200 + t), 33, C4_H, C4_D))) for t in range(sample)]
+    t0 = time.perf_counter()
+    ref = [oracle.train(X, y, p, float(np.float32(LR)), epochs)[0] for X, y, p in onets]
+    dt = time.perf_counter() - t0
+    dev = torch.device("cuda")
+    Xd = torch.from_numpy(Xh.astype(np.float32)).to(dev).to(torch.bfloat16)
+    yd = torch.from_numpy(yh.astype(np.float32)).to(dev)
+    params = [torch.from_numpy(p.flat().astype(np.float32)).to(dev) for _, _, p in onets]
+    descs = [B.mlp_net_desc(C4_H, int(ns[t]), Xd[int(offs[t]):].data_ptr(), yd[int(offs[t]):].data_ptr(),
+                            params[t].data_ptr(), None) for t in range(sample)]
+    plan = B.mlp_batch_create(B.MLP_BF16, B.MLP_ACT_SIGMOID, C4_D, descs, LR, 1)
+    B.mlp_batch_run(plan, epochs, torch.cuda.current_stream().cuda_stream)
+    assert B.mlp_batch_check(plan, torch.cuda.current_stream().cuda_stream) == B.MLP_OK, B.mlp_last_error()
+    B.mlp_batch_destroy(plan)
+    err = 0.0
+    for P, q, (_, _, p0) in zip(params, ref, onets):
+        dg, dr = P.cpu().numpy().astype(np.float64) - p0.flat(), q.flat() - p0.flat()
+        err = max(err, float(np.max(np.abs(dg - dr)) / np.max(np.abs(dr))))
+    cpu = {"value": rows * epochs / dt, "unit": "sample-steps/s", "cores": 1, "kind": "oracle",
+           "sample": "%d of the nets (%d rows), %d epochs (serial FP64 C oracle, one thread)" % (sample, rows, epochs),
+           **host_cpu()}
+    parity = {"nets": sample, "epochs": epochs, "measure": "max over nets of max |dw - dw*| / max |dw*|",
+              "value": err, "tolerance": 2e-2}
+    return cpu, parity
 
 
 def main():
