@@ -99,3 +99,36 @@ def test_tc_batch_is_deterministic_and_validates():
     with pytest.raises(B.MLPError) as e:
         B.mlp_batch_create(B.MLP_BF16, 0, D_PAD, [bad], 0.1, 1)
     assert e.value.status == B.MLP_EINVAL
+
+
+@pytest.mark.parametrize("D_real,D_pad", [(5, 8), (13, 16), (33, 40), (50, 56)])
+def test_one_epoch_gradient_over_input_widths(D_real, D_pad):
+    """Every supported width class of the many-nets plan, H = 128 and 256."""
+    import torch
+    nets, shapes = [], [(300, 128), (513, 256)]
+    for i, (n, H) in enumerate(shapes):
+        X = I.bf16_round(I.features(5000 + 10 * D_pad + i, n, D_real, D_pad))
+        y = (X[:, 0] + X[:, 1] > 0).astype(np.float32)
+        nets.append((X, y, I.init_weights(5100 + 10 * D_pad + i, D_real, H, D_pad)))
+    keep, descs, params = [], [], []
+    for X, y, W in nets:
+        Xd = dev(I.bf16_bits(X).view(np.int16))
+        yd = dev(y)
+        P = dev(np.concatenate([W[0].ravel(), W[1], W[2], W[3]]).astype(np.float32))
+        keep += [Xd, yd]
+        params.append(P)
+        descs.append(B.mlp_net_desc(W[0].shape[0], X.shape[0], Xd.data_ptr(), yd.data_ptr(), P.data_ptr(), 0))
+    b = B.mlp_batch_create(B.MLP_BF16, B.MLP_ACT_SIGMOID, D_pad, descs, 1.0, 1)
+    try:
+        B.mlp_batch_run(b, 1, stream())
+        assert B.mlp_batch_check(b, stream()) == B.MLP_OK, B.mlp_last_error()
+    finally:
+        B.mlp_batch_destroy(b)
+    for (X, y, W), P in zip(nets, params):
+        got = host(P).astype(np.float64)
+        g = flat(W) - got
+        ref = oracle.mse_gradients(X, y, Params(*W))
+        exp = np.concatenate([ref[0].ravel(), ref[1], ref[2], [ref[3]]])
+        assert rel_err_norm(g, exp) <= BF16_GRAD_TOL, (D_pad, W[0].shape[0])
+        H = W[0].shape[0]
+        assert np.all(got[:H * D_pad].reshape(H, D_pad)[:, D_real:] == 0.0)

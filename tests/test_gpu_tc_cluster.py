@@ -155,3 +155,26 @@ def test_wide_net_65536_row_subset_one_epoch():
     acc_gpu = (oracle.predict(X, unflat(got, H)) == y).mean()
     acc_ref = (oracle.predict(X, q) == y).mean()
     assert abs(acc_gpu - acc_ref) <= 0.01
+
+
+@pytest.mark.parametrize("D_real,D_pad", [(5, 8), (13, 16), (33, 40), (48, 48)])
+def test_one_step_gradient_over_input_widths(D_real, D_pad):
+    """Every supported width class: the forward covers D rounded up to 16
+    columns, the gradient MMA carries the ones column at column D."""
+    n, H = 700, 512
+    X = I.bf16_round(I.features(3700 + D_pad, n, D_real, D_pad))
+    y = (X[:, 0] + X[:, 1] > 0).astype(np.float32)
+    W = I.init_weights(3800 + D_pad, D_real, H, D_pad)
+    import torch
+    with Net(D_pad, H, 1.0, 1, B.MLP_BF16) as net:
+        net.set(W)
+        B.mlp_train_epochs(net.h, dev(I.bf16_bits(X).view(np.int16)), dev(y), n, 1, 0, None, None, stream())
+        assert net.check() == B.MLP_OK, B.mlp_last_error()
+        got = net.flat()
+    g = flat(W) - got
+    ref = oracle.mse_gradients(X, y, Params(*W))
+    exp = np.concatenate([ref[0].ravel(), ref[1], ref[2], [ref[3]]])
+    assert rel_err_norm(g, exp) <= BF16_GRAD_TOL
+    HD = H * D_pad
+    assert rel_err_norm(g[HD:HD + H], ref[1]) <= BF16_GRAD_TOL, "gb1"
+    assert np.all(got[:HD].reshape(H, D_pad)[:, D_real:] == 0.0)
