@@ -484,6 +484,8 @@ def run_c2(args, rank, world, local):
     plain = plain_rate(B, hp, Xall[int(offs_x[t_mid]):], yall[int(offs_x[t_mid]):], int(ns[t_mid]), 200, stream)
     B.mlp_destroy(hp)
     T_f = aggregate_max(sum(times), world)
+    rec = traffic_record("k_batched_train")
+    c2_traffic = rec["dram_bytes_per_launch"] if rec and rec.get("workload") == "c2" else None
     units = int(ns.sum()) * C2_EPOCHS * world
     flops = float(np.sum(ns * (4 * D_IN * Hs + 10 * Hs))) * C2_EPOCHS
     peak = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
@@ -495,7 +497,7 @@ def run_c2(args, rank, world, local):
         "config": {"workload": C2_WORKLOAD, "nets": C2_NETS, "rows_total": int(ns.sum()), "epochs_per_step": C2_EPOCHS,
                    "l2": "flushed between timed steps (256 MiB write, outside the timed intervals)"},
         "roofline": {"bound": "alu", "achieved": flops / launch_s / 1e12, "peak": peak, "unit": "TFLOP/s",
-                     "frac": flops / launch_s / 1e12 / peak, "traffic": None, "kernel": "k_batched_train<36,sigmoid>",
+                     "frac": flops / launch_s / 1e12 / peak, "traffic": c2_traffic, "kernel": "k_batched_train<36,sigmoid>",
                      "flops_per_launch": flops},
         "plain_fp32": {"value": plain, "unit": "sample-steps/s",
                        "path": "mlp_step_plain on one mid-size net of the workload (the plain path takes one net "
