@@ -74,6 +74,7 @@ template <int DP, int WU, int ACT>
 __global__ void __launch_bounds__(FNT, 2) k_fused_train(FArgs a) {
     extern __shared__ __align__(16) float smem[];
     __shared__ double s_red[RE_NW];
+    __shared__ long long s_sse;   // the step's fixed-point squared-error sum
     using Eng = RowEngine<DP, WU, ACT>;
     constexpr int NG = Eng::NG;
     const int D = a.D, H = a.H;
@@ -184,16 +185,18 @@ __global__ void __launch_bounds__(FNT, 2) k_fused_train(FArgs a) {
             // ---- every block applies the summed gradient to its own copy
             const bool want_gn = g == 0 && a.gnorm_hist && epoch_end;
             double gn = 0.0;
-            for (int base = 0; base < P; base += 12 * FNT) {
-                long long v[12];  // twelve loads in flight per thread: one round trip up to P = 3072
+            // the gradient and the squared error (entry P) in one round trip
+            for (int base = 0; base < P1; base += 12 * FNT) {
+                long long v[12];  // twelve loads in flight per thread: one round trip up to P = 3071
 #pragma unroll
                 for (int r = 0; r < 12; ++r) {
                     const int p = base + r * FNT + tid;
-                    v[r] = (p < P) ? __ldcg(acc + p) : 0ll;
+                    v[r] = (p < P1) ? __ldcg(acc + p) : 0ll;
                 }
 #pragma unroll
                 for (int r = 0; r < 12; ++r) {
                     const int p = base + r * FNT + tid;
+                    if (p == P) s_sse = v[r];
                     if (p < P) {
                         const float gsum = (float)v[r] * gscale;
                         Wm[p] -= a.lr * gsum;
@@ -210,7 +213,7 @@ __global__ void __launch_bounds__(FNT, 2) k_fused_train(FArgs a) {
                 }
                 __syncthreads();
                 if (tid == 0) {
-                    sse_epoch += (double)__ldcg(acc + P) * (1.0 / 4294967296.0);
+                    sse_epoch += (double)s_sse * (1.0 / 4294967296.0);
                     if (epoch_end) {
                         const double L = 0.5 * sse_epoch * Cl;
                         if (a.loss_hist) a.loss_hist[e] = L;
