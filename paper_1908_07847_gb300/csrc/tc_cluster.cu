@@ -7,9 +7,10 @@
 // takes the 128-row tiles k, k + K, ... (K clusters).  Per tile, every block of
 // the cluster loads the same X tile (TMA, 128-byte swizzle), computes its slice
 // of Z1 = X W1^T on the tensor cores, its share of z2 = h w2 (h = sigmoid), and
-// the blocks add their shares through distributed shared memory in a fixed
-// order (each block signals the others' mbarriers when its share is written);
-// every block then has z2, o, d2 for the tile, builds its slice of d1 and
+// pushes the share into every block's receive buffer in distributed shared
+// memory (st.async, completion counted by the receiver's mbarrier); each block
+// adds the shares in rank order, so all blocks of a cluster have the same z2,
+// o and d2 for the tile; every block then builds its slice of d1 and
 // accumulates its slice of gW1 | gb1 and gw2 in tensor memory (as in the
 // many-nets kernel, tc_kernels.cu).  At the end of the step the gradient is
 // summed over clusters by a reduce-scatter in global memory among the K blocks
