@@ -49,8 +49,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--nets", type=int, default=0, help="c4 only: number of nets (default 1024; fewer for profiling)")
     ap.add_argument("--epochs", type=int, default=0, help="c4 only: epochs per step (default 200)")
-    ap.add_argument("--workload", default="c1", choices=["c1", "c2", "c3", "c4"],
-                    help="c1: the 33-64-1 full-batch workload (default line); "
+    ap.add_argument("--workload", default="c1", choices=["c0", "c1", "c2", "c3", "c4"],
+                    help="c0: the 33-16-1 net on the 120-row cohort, 1000 epochs per step; "
+                         "c1: the 33-64-1 full-batch workload (default line); "
                          "c2: 4096 independent 33-H-1 nets, 500 epochs per step; "
                          "c3: one 48-2048-1 net on bf16 tensor cores, 1M rows, mini-batch 8192, one epoch per step; "
                          "c4: 1024 independent 48-256-1 nets on bf16 tensor cores, 200 epochs per step")
@@ -404,6 +405,149 @@ def run_reference(args, rank, world):
         "gpu_launches": 0,
     }
     print(json.dumps(out), flush=True)
+
+
+# ------------------------------------------------- cohort workload (c0) ----
+
+C0_ROWS, C0_TRAIN, C0_H, C0_EPOCHS = 120, 96, 16, 1000
+C0_WORKLOAD = ("33-16-1 sigmoid MLP on the 120-row synthetic cohort (first 96 rows train, 24 test), "
+               "full-batch GD lr 0.1, 1000 epochs per step in one launch, FP32")
+
+
+def run_c0(args, rank, world, local):
+    """The cohort-sized network (Sec. 2.1-2.2 sizes): every step trains the
+    33-16-1 net from the same initial weights for 1000 full-batch epochs on
+    the 96 training rows, in one launch of the fused kernel (the rows stay in
+    shared memory for all epochs)."""
+    import torch
+    from paper_1908_07847_gb300 import binding as B
+    from paper_1908_07847_gb300 import inputs as I
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream().cuda_stream
+    X = I.features(I.COHORT_SEED + 1000 * rank, C0_ROWS)
+    W = I.init_weights(I.INIT_SEED + rank, D_IN, C0_H)
+    T = I.teacher_weights(D=D_IN)
+    Xd = torch.from_numpy(X).to(dev)
+    th = B.mlp_create(D_IN, T[0].shape[0], LR, 1, B.MLP_FP32, B.MLP_ACT_SIGMOID)
+    B.mlp_set_weights(th, *T)
+    lab = torch.zeros(C0_ROWS, dtype=torch.int8, device=dev)
+    B.mlp_predict(th, Xd, C0_ROWS, lab, stream)
+    B.mlp_destroy(th)
+    yd = lab.to(torch.float32)
+    Xtr, ytr = Xd[:C0_TRAIN].contiguous(), yd[:C0_TRAIN].contiguous()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    lh = torch.zeros(C0_EPOCHS, dtype=torch.float64, device=dev)
+    h = B.mlp_create(D_IN, C0_H, LR, 1, B.MLP_FP32, B.MLP_ACT_SIGMOID)
+    # rows per block: the fastest of a few splits for 100-epoch launches (untimed)
+    per_epoch = {}
+    for rows in (96, 48, 32, 24, 16, 12, 8):
+        B.mlp_set_rows_per_block(h, rows)
+        B.mlp_set_weights(h, *W)
+        B.mlp_train_epochs(h, Xd[:C0_TRAIN], yd[:C0_TRAIN], C0_TRAIN, 100, 0, None, None, stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        B.mlp_train_epochs(h, Xd[:C0_TRAIN], yd[:C0_TRAIN], C0_TRAIN, 100, 0, None, None, stream)
+        e1.record()
+        torch.cuda.synchronize()
+        per_epoch[rows] = e0.elapsed_time(e1) * 10.0   # us per epoch
+    rows_best = min(per_epoch, key=per_epoch.get)
+    B.mlp_set_rows_per_block(h, rows_best)
+
+    def timed(step_fn, steps, warmup):
+        # every step restarts from the initial weights (set outside the timed interval)
+        for _ in range(warmup):
+            B.mlp_set_weights(h, *W)
+            step_fn()
+        torch.cuda.synchronize()
+        out = []
+        for _ in range(steps):
+            B.mlp_set_weights(h, *W)
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            step_fn()
+            e1.record()
+            torch.cuda.synchronize()
+            out.append(e0.elapsed_time(e1) * 1e-3)
+        return out
+
+    def fused_step():
+        B.mlp_train_epochs(h, Xtr, ytr, C0_TRAIN, C0_EPOCHS, 0, lh, None, stream)
+
+    def plain_step():
+        for _ in range(C0_EPOCHS):
+            B.mlp_step_plain(h, Xtr, ytr, C0_TRAIN, lh, stream)
+
+    Xh = torch.from_numpy(np.ascontiguousarray(X[:C0_TRAIN])).pin_memory()
+    yh = ytr.cpu().pin_memory()
+    lhh = torch.zeros(C0_EPOCHS, dtype=torch.float64).pin_memory()
+
+    def e2e_step():
+        B.mlp_train_host(h, Xh, yh, C0_TRAIN, C0_EPOCHS, 0, lhh, stream)
+
+    barrier(world)
+    with ClockSampler(local) as clk:
+        t_fused = timed(fused_step, args.steps, args.warmup)
+    # accuracies after one step (1000 epochs from the initial weights)
+    pred = torch.zeros(C0_ROWS, dtype=torch.int8, device=dev)
+    B.mlp_predict(h, Xd, C0_ROWS, pred, stream)
+    torch.cuda.synchronize()
+    ok = (pred == lab).cpu().numpy()
+    acc = {"train": float(ok[:C0_TRAIN].mean()), "test": float(ok[C0_TRAIN:].mean())}
+    t_plain = timed(plain_step, max(2, args.steps // 10), 1)
+    t_e2e = timed(e2e_step, max(3, args.steps // 4), 1)
+    assert B.mlp_check(h, stream) == B.MLP_OK, B.mlp_last_error()
+    B.mlp_destroy(h)
+    barrier(world)
+    T_f = aggregate_max(sum(t_fused), world)
+    T_p = aggregate_max(sum(t_plain), world)
+    T_e = aggregate_max(sum(t_e2e), world)
+    units = C0_TRAIN * C0_EPOCHS * world
+    flops = (4 * D_IN * C0_H + 10 * C0_H) * C0_TRAIN * C0_EPOCHS
+    launch_s = statistics.mean(t_fused)
+    peak = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    out = {
+        "metric": METRIC, "value": units * args.steps / T_f, "unit": "sample-steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": T_f / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": C0_WORKLOAD, "n": C0_ROWS, "n_train": C0_TRAIN, "D": D_IN, "H": C0_H, "lr": LR,
+                   "epochs_per_step": C0_EPOCHS, "rows_per_block": rows_best, "us_per_epoch": T_f / args.steps / C0_EPOCHS * 1e6,
+                   "l2": "flushed between timed steps (256 MiB write, outside the timed intervals)"},
+        "accuracy": acc,
+        "plain_fp32": {"value": units * len(t_plain) / T_p, "unit": "sample-steps/s",
+                       "ms_per_step": T_p / len(t_plain) * 1e3,
+                       "path": "mlp_step_plain, one call (five kernels) per epoch",
+                       "speedup_of_fused": (units * args.steps / T_f) / (units * len(t_plain) / T_p)},
+        "e2e": {"value": units * len(t_e2e) / T_e, "unit": "sample-steps/s",
+                "h2d_bytes_per_step": C0_TRAIN * D_IN * 4 + C0_TRAIN * 4, "d2h_bytes_per_step": 8 * C0_EPOCHS,
+                "call": "mlp_train_host (pinned host X, y in; loss history out)"},
+        "roofline": {"bound": "alu", "achieved": flops / launch_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+                     "frac": flops / launch_s / 1e12 / peak, "traffic": None, "kernel": "k_fused_train (33-16-1 instance)",
+                     "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (FFMA, derived)",
+                     "flops_per_launch": flops},
+        "gpu_launches": args.steps, "clocks": clk.summary(),
+    }
+    if rank == 0:
+        out["cpu_baseline"], out["parity"] = c0_oracle_leg(X, W, T, acc)
+        print(json.dumps(out), flush=True)
+
+
+def c0_oracle_leg(X, W, T, acc_gpu):
+    """The FP64 oracle's full run of the workload (1000 epochs, one thread),
+    timed; its train and test accuracies beside the library's."""
+    import oracle
+    y = oracle.predict(X, oracle.Params(*T)).astype(np.float64)
+    t0 = time.perf_counter()
+    q, _, _ = oracle.train(X[:C0_TRAIN], y[:C0_TRAIN], oracle.Params(*W), float(np.float32(LR)), C0_EPOCHS)
+    dt = time.perf_counter() - t0
+    ok = oracle.predict(X, q) == y
+    cpu = {"value": C0_TRAIN * C0_EPOCHS / dt, "unit": "sample-steps/s", "cores": 1, "kind": "oracle",
+           "sample": "the whole step: 1000 full-batch epochs over the 96 training rows (serial FP64 C oracle)",
+           **host_cpu()}
+    parity = {"oracle_accuracy": {"train": float(ok[:C0_TRAIN].mean()), "test": float(ok[C0_TRAIN:].mean())},
+              "accuracy": acc_gpu, "tolerance": "one point (0.01) of the oracle's"}
+    return cpu, parity
 
 
 # ------------------------------------------------- many-nets workload (c2) --
@@ -853,6 +997,8 @@ def main():
         dist.init_process_group("nccl")
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload == "c0":
+        run_c0(args, rank, world, local)
     elif args.workload == "c2":
         run_c2(args, rank, world, local)
     elif args.workload == "c3":

@@ -186,7 +186,10 @@ mlp_status mlp_backward_w(int32_t prec, int32_t act, int32_t D, int32_t H, int64
  * records MLP_ETIMEOUT (read it with mlp_check).  -1 restores normal runs. */
 mlp_status mlp_debug_skip_block(mlp_t net, int32_t skip_block);
 
-/* Rows per block of the fused training kernel (tuning knob, default 32). */
+/* Rows per block of the fused training kernel (tuning knob, default 32).  When
+ * a step's rows fit one block, the launch is a single block that sums and
+ * updates on chip (no cross-block accumulator or barrier); the result follows
+ * the same fixed-point rounding of the gradient as a multi-block launch. */
 mlp_status mlp_set_rows_per_block(mlp_t net, int32_t rows);
 
 /*

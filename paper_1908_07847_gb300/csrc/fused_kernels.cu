@@ -75,6 +75,7 @@ __global__ void __launch_bounds__(FNT, 2) k_fused_train(FArgs a) {
     extern __shared__ __align__(16) float smem[];
     __shared__ double s_red[RE_NW];
     __shared__ long long s_sse;   // the step's fixed-point squared-error sum
+    __shared__ double s_gn[RE_NW];
     using Eng = RowEngine<DP, WU, ACT>;
     constexpr int NG = Eng::NG;
     const int D = a.D, H = a.H;
@@ -161,6 +162,50 @@ __global__ void __launch_bounds__(FNT, 2) k_fused_train(FArgs a) {
             // ---- block partial, in fixed point, into the global accumulator
             eng.write_group(gpart, s_red);
             __syncthreads();
+            if (G == 1) {
+                // A single block holds the whole step: its partial is the sum.  The
+                // same fixed-point rounding as the cross-block path, applied here,
+                // without the global accumulator, the barrier or the counters.
+                if (status0 & ST_TIMEOUT) return;
+                const bool want_gn = a.gnorm_hist && epoch_end;
+                double gn = 0.0;
+                int bad = 0;
+                for (int p = tid; p < P; p += FNT) {
+                    float s = gpart[p];
+#pragma unroll
+                    for (int q = 1; q < NG; ++q) s += gpart[q * P + p];
+                    const float v = s * gup;
+                    if (!(fabsf(v) < 4.0e18f)) bad = 1;
+                    const float gsum = (float)__float2ll_rn(v) * gscale;
+                    Wm[p] -= a.lr * gsum;
+                    if (want_gn) gn = fma((double)gsum, (double)gsum, gn);
+                }
+                if (bad) atomicOr(a.status, ST_NONFINITE);
+                if (want_gn) {
+                    gn = warp_sum(gn);
+                    if ((tid & 31) == 0) s_gn[tid >> 5] = gn;
+                }
+                __syncthreads();
+                if (tid == 0) {
+                    double t = 0.0;
+                    for (int q = 0; q < NG; ++q) t += s_red[q];
+                    const double v = t * 4294967296.0;
+                    if (!(v < 4.0e18)) atomicOr(a.status, ST_NONFINITE);
+                    sse_epoch += (double)__double2ll_rn(v) * (1.0 / 4294967296.0);
+                    if (epoch_end) {
+                        const double L = 0.5 * sse_epoch * Cl;
+                        if (a.loss_hist) a.loss_hist[e] = L;
+                        if (!isfinite(L)) atomicOr(a.status, ST_NONFINITE);
+                        if (want_gn) {
+                            double u = 0.0;
+                            for (int q = 0; q < RE_NW; ++q) u += s_gn[q];
+                            a.gnorm_hist[e] = sqrt(u);
+                        }
+                    }
+                }
+                __syncthreads();
+                continue;
+            }
             int bad = 0;
             for (int p = tid; p < P; p += FNT) {
                 float s = gpart[p];
@@ -293,7 +338,21 @@ int blocks_per_sm(void *fn, size_t smem, cudaError_t *err) {
             if (cache[i].fn == fn && cache[i].smem == smem && cache[i].dev == dev) return cache[i].per_sm;
     }
     if (smem > 48 * 1024) {
-        *err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        // Raise the kernel's ceiling to the device's opt-in limit rather than to
+        // this request: a cached entry for a larger request must not find the
+        // ceiling lowered by a smaller one made since.
+        // (the limit covers the kernel's static shared memory as well)
+        int optin = 0;
+        cudaFuncAttributes fa;
+        *err = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (*err == cudaSuccess) *err = cudaFuncGetAttributes(&fa, fn);
+        if (*err != cudaSuccess) return 0;
+        const size_t ceiling = (size_t)optin - fa.sharedSizeBytes;
+        if (smem > ceiling) {
+            *err = cudaErrorInvalidValue;
+            return 0;
+        }
+        *err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ceiling);
         if (*err != cudaSuccess) return 0;
     }
     int per_sm = 0;
@@ -389,8 +448,11 @@ cudaError_t fused_train(int act, int D, int H, int64_t n, const float *X, const 
     e = cudaLaunchCooperativeKernel(ch.fn, dim3((unsigned)G), dim3(FNT), args, smem, st);
     if (e != cudaSuccess) return e;
     // One barrier per step for every block; the accumulator rotates by a step.
-    ctr->bar += (unsigned long long)G * (unsigned long long)steps;
-    ctr->rot = (int)((ctr->rot + steps) % 3);
+    // A single block uses neither (it sums and updates on chip).
+    if (G > 1) {
+        ctr->bar += (unsigned long long)G * (unsigned long long)steps;
+        ctr->rot = (int)((ctr->rot + steps) % 3);
+    }
     return cudaSuccess;
 }
 

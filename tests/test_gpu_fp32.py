@@ -310,3 +310,52 @@ def test_fp32_sigmoid_error_bound():
                     stream())
     r = host(h3)[:, 0]
     assert r[0] == 1.0 and r[1] == 0.0 and np.isnan(r[2])
+
+
+@pytest.mark.parametrize("n,D,H,mb", [(96, 33, 16, 0), (200, 33, 64, 0), (300, 7, 33, 100), (1, 1, 1, 0)])
+def test_single_block_path_matches_oracle(n, D, H, mb):
+    """A grid of one block (rows per block >= the rows of a step) sums and
+    updates on chip: weights, loss and gradient-norm histories against the
+    oracle, for full batch and mini-batches."""
+    X, y, W = problem(1500 + n, n, D, H)
+    t = torch()
+    epochs = 50
+    with Net(D, H) as net:
+        net.set(W)
+        B.mlp_set_rows_per_block(net.h, 512)
+        lh = t.zeros(epochs, dtype=t.float64, device="cuda")
+        gh = t.zeros(epochs, dtype=t.float64, device="cuda")
+        B.mlp_train_epochs(net.h, dev(X), dev(y), n, epochs, mb, lh, gh, stream())
+        assert net.check() == B.MLP_OK, B.mlp_last_error()
+        q, lh_ref, gh_ref = oracle.train(X, y, Params(*W), lr32(), epochs, minibatch=mb)
+        assert rel_err_norm(net.flat(), q.flat()) <= W_TOL
+        assert rel_err_elem(host(lh), lh_ref) <= 1e-5
+        assert rel_err_elem(host(gh), gh_ref) <= 1e-4
+
+
+def test_single_block_then_multi_block_on_one_handle():
+    """The one-block path leaves the cross-block counters alone: a multi-block
+    launch after it (and after it again) still meets its barriers, and the
+    result is the oracle's for the whole schedule."""
+    n, D, H = 700, 33, 64
+    X, y, W = problem(1600, n, D, H)
+    Xd, yd = dev(X), dev(y)
+    with Net(D, H) as net:
+        net.set(W)
+        for rows in (1024, 32, 1024, 32):
+            B.mlp_set_rows_per_block(net.h, rows)
+            B.mlp_train_epochs(net.h, Xd, yd, n, 3, 0, None, None, stream())
+            assert net.check() == B.MLP_OK, (rows, B.mlp_last_error())
+        q, _, _ = oracle.train(X, y, Params(*W), lr32(), 12)
+        assert rel_err_norm(net.flat(), q.flat()) <= W_TOL
+
+
+def test_single_block_path_reports_nonfinite():
+    n, D, H = 64, 4, 8
+    X, y, W = problem(1700, n, D, H)
+    X[5, 2] = np.nan
+    with Net(D, H) as net:
+        net.set(W)
+        B.mlp_set_rows_per_block(net.h, 64)
+        B.mlp_train_epochs(net.h, dev(X), dev(y), n, 1, 0, None, None, stream())
+        assert net.check() == B.MLP_ENONFINITE
