@@ -31,12 +31,13 @@ __host__ __device__ inline int re_wu(int H) { return H <= 32 ? 1 : (H <= 64 ? 2 
 // Row groups per block.
 __host__ __device__ inline int re_groups(int H) { return RE_NW / re_wu(H); }
 
-template <int DP, int WU, int ACT>
+// RB1: rows in flight per lane when H <= 32 (segments of a warp already take
+// separate rows there); a kernel with the register file to itself can afford
+// more than the default two.
+template <int DP, int WU, int ACT, int RB1 = 2>
 struct RowEngine {
     static constexpr int NG = RE_NW / WU;
-    // Rows in flight per lane: segments of a warp already take separate rows
-    // when H <= 32, so two per lane keep the register budget there.
-    static constexpr int RB = (WU == 1) ? 2 : RE_RB;
+    static constexpr int RB = (WU == 1) ? RB1 : RE_RB;
     // Per-lane state: the neuron's weights and gradient sums.
     float w[DP];
     float acc[DP];
