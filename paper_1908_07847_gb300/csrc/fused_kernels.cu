@@ -70,19 +70,19 @@ __device__ __forceinline__ void red_add(long long *p, long long v) {
     asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-// Two blocks per SM, except for H <= 32 (WU = 1): there each lane keeps whole
-// rows in registers and one block per SM (the fused grid rarely needs more than
-// one wave) lets it keep three rows in flight without spilling (D <= 36).
+// One block per SM (the fused grid rarely needs more than one wave): with the
+// register file to itself a lane keeps eight rows in flight for H > 32, and
+// three for H <= 32 with D <= 36, without spilling.
 template <int DP, int WU>
 __host__ __device__ constexpr int fused_rb1() { return (WU == 1 && DP <= 36) ? 3 : 2; }
 
 template <int DP, int WU, int ACT>
-__global__ void __launch_bounds__(FNT, WU == 1 ? 1 : 2) k_fused_train(FArgs a) {
+__global__ void __launch_bounds__(FNT, 1) k_fused_train(FArgs a) {
     extern __shared__ __align__(16) float smem[];
     __shared__ double s_red[RE_NW];
     __shared__ long long s_sse;   // the step's fixed-point squared-error sum
     __shared__ double s_gn[RE_NW];
-    using Eng = RowEngine<DP, WU, ACT, fused_rb1<DP, WU>()>;
+    using Eng = RowEngine<DP, WU, ACT, fused_rb1<DP, WU>(), 8>;
     constexpr int NG = Eng::NG;
     const int D = a.D, H = a.H;
     const int P = (D + 2) * H + 1;
@@ -343,11 +343,11 @@ int blocks_per_sm(void *fn, size_t smem, cudaError_t *err) {
         for (int i = 0; i < ncache; ++i)
             if (cache[i].fn == fn && cache[i].smem == smem && cache[i].dev == dev) return cache[i].per_sm;
     }
-    if (smem > 48 * 1024) {
+    {
         // Raise the kernel's ceiling to the device's opt-in limit rather than to
         // this request: a cached entry for a larger request must not find the
-        // ceiling lowered by a smaller one made since.
-        // (the limit covers the kernel's static shared memory as well)
+        // ceiling lowered by a smaller one made since.  Always: the default
+        // ceiling (48 KB) covers the kernel's static shared memory as well.
         int optin = 0;
         cudaFuncAttributes fa;
         *err = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);

@@ -23,21 +23,23 @@ namespace mlp {
 
 constexpr int RE_NW = 8;               // warps per block
 constexpr int RE_NT = RE_NW * 32;      // threads per block
-constexpr int RE_RB = 4;               // rows per lane per iteration
-constexpr int RE_ZX = 2 * RE_NW * RE_RB;  // floats of z2 exchange space
+constexpr int RE_RB = 4;               // rows per lane per iteration (default)
+constexpr int RE_RB_MAX = 8;           // most rows per lane any kernel asks for
+constexpr int RE_ZX = 2 * RE_NW * RE_RB_MAX;  // floats of z2 exchange space
 
 // Warps per row group for a width H (1, 2 or 4).
 __host__ __device__ inline int re_wu(int H) { return H <= 32 ? 1 : (H <= 64 ? 2 : 4); }
 // Row groups per block.
 __host__ __device__ inline int re_groups(int H) { return RE_NW / re_wu(H); }
 
-// RB1: rows in flight per lane when H <= 32 (segments of a warp already take
-// separate rows there); a kernel with the register file to itself can afford
-// more than the default two.
-template <int DP, int WU, int ACT, int RB1 = 2>
+// Rows in flight per lane: RB1 when H <= 32 (segments of a warp already take
+// separate rows there), RBN otherwise; a kernel with the register file to
+// itself can afford more than the defaults.
+template <int DP, int WU, int ACT, int RB1 = 2, int RBN = RE_RB>
 struct RowEngine {
+    static_assert(RB1 <= RE_RB_MAX && RBN <= RE_RB_MAX, "z2 exchange space");
     static constexpr int NG = RE_NW / WU;
-    static constexpr int RB = (WU == 1) ? RB1 : RE_RB;
+    static constexpr int RB = (WU == 1) ? RB1 : RBN;
     // Per-lane state: the neuron's weights and gradient sums.
     float w[DP];
     float acc[DP];
