@@ -324,7 +324,8 @@ def run_ours(args, rank, world, local):
                        "speedup_of_fused": value / plain_value},
         "e2e": {"value": e2e_value, "unit": "sample-steps/s",
                 "h2d_bytes_per_step": N_ROWS * D_IN * 4 + N_ROWS * 4, "d2h_bytes_per_step": 8,
-                "call": "mlp_train_host (pinned host X, y in; loss out)"},
+                "call": "mlp_train_host (pinned host X, y in, read by the kernel through the host mapping; "
+                        "loss written back to pinned host memory)"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic_from_profile(),
                      "kernel": "k_fused_train<36,2,sigmoid>",

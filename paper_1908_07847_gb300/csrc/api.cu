@@ -79,6 +79,16 @@ struct DeviceScope {
     }
 };
 
+// The device address of page-locked host memory, or NULL for pageable memory.
+const void *mapped_host(const void *p) {
+    cudaPointerAttributes a;
+    if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 mlp_status grow(void **p, size_t *cap, size_t need, const char *what) {
     if (need <= *cap && *p) return MLP_OK;
     if (*p) cudaFree(*p);
@@ -374,6 +384,21 @@ mlp_status mlp_train_host(mlp_t h, const void *X_host, const void *y_host, int64
         return fail(MLP_EINVAL, "mlp_train_host: bad arguments");
     DeviceScope ds(h->device);
     cudaStream_t st = (cudaStream_t)stream;
+    if (epochs == 1 && n > 0 && h->cfg.prec != MLP_BF16) {
+        // One epoch reads every row once: page-locked host buffers are read where
+        // they are, through the device's mapping of them (over NVLink-C2C on a
+        // Grace-Blackwell node), and the loss is written straight back, instead
+        // of staging copies that only add their latency.  The bf16 paths load
+        // X by TMA from device memory and always stage.
+        const void *Xm = mapped_host(X_host), *ym = mapped_host(y_host);
+        double *lm = loss_hist_host ? (double *)mapped_host(loss_hist_host) : nullptr;
+        if (Xm && ym && (!loss_hist_host || lm)) {
+            mlp_status s = mlp_train_epochs(h, Xm, ym, n, 1, minibatch, lm, nullptr, stream);
+            if (s) return s;
+            CK(cudaStreamSynchronize(st), "mlp_train_host sync");
+            return MLP_OK;
+        }
+    }
     const size_t xb = x_elem_bytes(h->cfg.prec) * (size_t)h->cfg.D * (size_t)n;
     const size_t yb = h->esz * (size_t)n;
     mlp_status s = grow(&h->xstage, &h->xstage_cap, xb, "X staging");

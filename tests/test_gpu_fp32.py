@@ -359,3 +359,28 @@ def test_single_block_path_reports_nonfinite():
         B.mlp_set_rows_per_block(net.h, 64)
         B.mlp_train_epochs(net.h, dev(X), dev(y), n, 1, 0, None, None, stream())
         assert net.check() == B.MLP_ENONFINITE
+
+
+@pytest.mark.parametrize("mb", [0, 1000])
+def test_host_entry_reads_page_locked_buffers_in_place(mb):
+    """One-epoch calls on page-locked host buffers (read through the device's
+    mapping, no staging copy) give the device entry's weights and losses bit
+    for bit; pageable buffers take the staging copy and agree as well."""
+    n, D, H = 4096, 33, 64
+    X, y, W = problem(1800 + mb, n, D, H)
+    t = torch()
+    Xp = t.from_numpy(X).pin_memory()
+    yp = t.from_numpy(y).pin_memory()
+    lp = t.zeros(1, dtype=t.float64).pin_memory()
+    with Net(D, H) as a, Net(D, H) as b, Net(D, H) as c:
+        for net in (a, b, c):
+            net.set(W)
+        lhd = t.zeros(1, dtype=t.float64, device="cuda")
+        lpg = np.zeros(1)
+        for _ in range(3):
+            B.mlp_train_host(a.h, Xp, yp, n, 1, mb, lp, stream())
+            B.mlp_train_epochs(b.h, dev(X), dev(y), n, 1, mb, lhd, None, stream())
+            B.mlp_train_host(c.h, X, y, n, 1, mb, lpg, stream())
+            assert float(lp[0]) == float(host(lhd)[0]) == float(lpg[0])
+        assert a.check() == B.MLP_OK
+        assert np.array_equal(a.flat(), b.flat()) and np.array_equal(c.flat(), b.flat())
