@@ -390,7 +390,13 @@ __global__ void __launch_bounds__(NT, 1) k_tc_batched(TcArgs a) {
                     sse_t += (double)red[2 * w];
                     gb2 += red[2 * w + 1];
                 }
-                // hidden unit of this thread: block hb = half (H = 256) or 0 (H = 128)
+                // The gradient rows go to shared memory (the h^T buffer is free
+                // once every MMA of the epoch has completed) so that the FP32
+                // master weights in global memory are updated with coalesced
+                // accesses: a row per thread there would touch a cache line per
+                // lane and load.  Hidden unit of this thread: block hb = half
+                // (H = 256) or 0 (H = 128).
+                float *gs = (float *)(sm + SM_HT);   // H x D gradient, row-major
                 if (half < H / 128) {
                     const int hb = half;
                     const int j = hb * 128 + r;  // hidden unit = lane
@@ -399,18 +405,11 @@ __global__ void __launch_bounds__(NT, 1) k_tc_batched(TcArgs a) {
 #pragma unroll
                     for (int c16 = 0; c16 < 64; c16 += 16) {
                         if (c16 >= D) break;
-                        float g[16], w[16];
+                        float g[16];
                         tmem_ld16(lane_base + TM_GW1 + 64 * hb + c16, g);
 #pragma unroll
                         for (int u = 0; u < 16; ++u)
-                            if (c16 + u < D) w[u] = P[j * D + c16 + u];
-#pragma unroll
-                        for (int u = 0; u < 16; ++u)
-                            if (c16 + u < D) {
-                                w[u] -= a.lr * g[u];
-                                P[j * D + c16 + u] = w[u];
-                                *(__nv_bfloat16 *)(sm + SM_W1 + kmajor_off(j, c16 + u)) = __float2bfloat16_rn(0.5f * w[u]);
-                            }
+                            if (c16 + u < D) gs[j * D + c16 + u] = g[u];
                     }
                     const float nb1 = b1s[j] - a.lr * gb1;
                     const float nw2 = w2s[j] - a.lr * gw2;
@@ -420,6 +419,29 @@ __global__ void __launch_bounds__(NT, 1) k_tc_batched(TcArgs a) {
                     w2s[j] = nw2;
                     w2b[j] = __float2bfloat16_rn(nw2);
                     *(__nv_bfloat16 *)(sm + SM_B1T + k16_off(j, 0)) = __float2bfloat16_rn(0.5f * nb1);
+                }
+                if (!epi_sync()) { ok = false; break; }
+                {
+                    // w -= lr g over the flat H x D array, 16 loads in flight per thread
+                    const int et = (warp - 2) * 32 + lane;   // epilogue thread 0..255
+                    for (int i0 = et; i0 < HD; i0 += (int)NEPI_T * 16) {
+                        float w[16];
+#pragma unroll
+                        for (int v = 0; v < 16; ++v) {
+                            const int i = i0 + v * (int)NEPI_T;
+                            w[v] = i < HD ? P[i] : 0.f;
+                        }
+#pragma unroll
+                        for (int v = 0; v < 16; ++v) {
+                            const int i = i0 + v * (int)NEPI_T;
+                            if (i < HD) {
+                                const int j = i / D, k = i - j * D;
+                                w[v] -= a.lr * gs[i];
+                                P[i] = w[v];
+                                *(__nv_bfloat16 *)(sm + SM_W1 + kmajor_off(j, k)) = __float2bfloat16_rn(0.5f * w[v]);
+                            }
+                        }
+                    }
                 }
                 b2 -= a.lr * gb2;
                 if (half == 0 && r == 0) {
