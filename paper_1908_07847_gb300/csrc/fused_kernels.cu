@@ -20,7 +20,9 @@
 //   4. the accumulator is triple-buffered: while reading buffer s, each block
 //      clears its share of buffer s + 2, which the barrier of step s + 1 then
 //      publishes before anyone adds into it.
-// At the end block 0 writes its copy of the weights back.
+// A grid of one block skips 2-4: it rounds its own partial the same way and
+// updates in shared memory.  At the end block 0 writes its copy of the weights
+// back.
 #include <mutex>
 
 #include "row_engine.cuh"
