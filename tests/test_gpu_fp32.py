@@ -384,3 +384,35 @@ def test_host_entry_reads_page_locked_buffers_in_place(mb):
             assert float(lp[0]) == float(host(lhd)[0]) == float(lpg[0])
         assert a.check() == B.MLP_OK
         assert np.array_equal(a.flat(), b.flat()) and np.array_equal(c.flat(), b.flat())
+
+
+@pytest.mark.parametrize("prec,D,H", [(B.MLP_FP32, 33, 64), (B.MLP_FP64, 33, 16), (B.MLP_BF16, 48, 512)])
+def test_empty_inputs_and_zero_epochs(prec, D, H):
+    """n = 0 trains nothing and reports zero losses; epochs = 0 touches
+    nothing; forward and predict of no rows succeed; negative sizes are
+    rejected.  Every path: fused FP32, plain FP64, tensor-core bf16."""
+    t = torch()
+    _, _, W = problem(1900 + prec, 8, D, H)
+    with Net(D, H, prec=prec) as net:
+        net.set(W)
+        before = net.flat()
+        lh = t.full((4,), 7.0, dtype=t.float64, device="cuda")
+        dummy = t.zeros(16, device="cuda")
+        B.mlp_train_epochs(net.h, dummy, dummy, 0, 4, 0, lh, None, stream())
+        assert net.check() == B.MLP_OK
+        assert np.all(host(lh) == 0.0)
+        lh.fill_(7.0)
+        B.mlp_train_epochs(net.h, dummy, dummy, 5, 0, 0, lh, None, stream())
+        assert np.all(host(lh) == 7.0)
+        assert np.array_equal(net.flat(), before)
+        o = t.zeros(1, device="cuda")
+        B.mlp_forward(net.h, dummy, 0, o, stream())
+        lab = t.zeros(1, dtype=t.int8, device="cuda")
+        B.mlp_predict(net.h, dummy, 0, lab, stream())
+        lhh = np.full(2, 7.0)
+        B.mlp_train_host(net.h, np.zeros(1, np.float32), np.zeros(1, np.float32), 0, 2, 0, lhh, stream())
+        assert np.all(lhh == 0.0)
+        assert np.array_equal(net.flat(), before)
+        with pytest.raises(B.MLPError) as e:
+            B.mlp_train_epochs(net.h, dummy, dummy, -1, 1, 0, None, None, stream())
+        assert e.value.status == B.MLP_EINVAL
