@@ -132,3 +132,51 @@ def test_one_epoch_gradient_over_input_widths(D_real, D_pad):
         assert rel_err_norm(g, exp) <= BF16_GRAD_TOL, (D_pad, W[0].shape[0])
         H = W[0].shape[0]
         assert np.all(got[:H * D_pad].reshape(H, D_pad)[:, D_real:] == 0.0)
+
+
+def test_config_1024_nets_sampled():
+    """The 1024-net workload at full size (48-256-1, n ~ U{4096..16384}, 10.5M
+    bf16 rows) in one launch of the plan, two epochs; four nets (the first,
+    the largest, the smallest, the last) against the oracle's run of the same
+    two epochs: loss history within 2e-2, weight change within 4e-2."""
+    import torch
+    seed, n_nets, D, H, epochs = 4, 1024, 48, 256, 2
+    _, ns = I.batched_shapes(seed, n_nets, (H, H), (4096, 16384))
+    offs = np.concatenate([[0], np.cumsum(ns)]).astype(np.int64)
+    total = int(offs[-1])
+    picks = sorted({0, int(np.argmax(ns)), int(np.argmin(ns)), n_nets - 1})
+    Xd = torch.zeros((total, D), dtype=torch.bfloat16, device="cuda")
+    yd = torch.zeros(total, dtype=torch.float32, device="cuda")
+    keep = {t: [] for t in picks}
+    chunk = 1 << 20
+    for r0 in range(0, total, chunk):
+        r1 = min(total, r0 + chunk)
+        Xc = I.bf16_round(I.features(I.subseed(seed, 10_000 + r0 // chunk), r1 - r0, D_REAL, D))
+        yc = (Xc[:, 0] + Xc[:, 1] > 0).astype(np.float32)
+        Xd[r0:r1] = torch.from_numpy(I.bf16_bits(Xc).view(np.int16)).to("cuda").view(torch.bfloat16)
+        yd[r0:r1] = torch.from_numpy(yc).to("cuda")
+        for t in picks:
+            a, b = max(int(offs[t]), r0), min(int(offs[t + 1]), r1)
+            if a < b:
+                keep[t].append((Xc[a - r0:b - r0].astype(np.float64), yc[a - r0:b - r0].astype(np.float64)))
+    W = [I.init_weights(I.subseed(seed, 200 + t), D_REAL, H, D) for t in range(n_nets)]
+    P = torch.from_numpy(np.concatenate([np.concatenate([np.ravel(a) for a in w]) for w in W]).astype(np.float32)).cuda()
+    Pp = (D + 2) * H + 1
+    L = torch.zeros((n_nets, epochs), dtype=torch.float64, device="cuda")
+    descs = [B.mlp_net_desc(H, int(ns[t]), Xd[int(offs[t]):].data_ptr(), yd[int(offs[t]):].data_ptr(),
+                            P[t * Pp:].data_ptr(), L[t].data_ptr()) for t in range(n_nets)]
+    b = B.mlp_batch_create(B.MLP_BF16, B.MLP_ACT_SIGMOID, D, descs, lr32(), 1)
+    try:
+        B.mlp_batch_run(b, epochs, stream())
+        assert B.mlp_batch_check(b, stream()) == B.MLP_OK, B.mlp_last_error()
+    finally:
+        B.mlp_batch_destroy(b)
+    Ph, Lh = host(P).astype(np.float64), host(L)
+    for t in picks:
+        X = np.concatenate([x for x, _ in keep[t]])
+        y = np.concatenate([v for _, v in keep[t]])
+        assert X.shape[0] == ns[t]
+        q, lh, _ = oracle.train(X, y, Params(*W[t]), lr32(), epochs)
+        w0 = flat(W[t])
+        assert rel_err_elem(Lh[t], lh) <= BF16_GRAD_TOL, t
+        assert rel_err_norm(Ph[t * Pp:(t + 1) * Pp] - w0, q.flat() - w0) <= 2 * BF16_GRAD_TOL, t
