@@ -201,10 +201,10 @@ def sfu_roofline(sigmoids_per_launch, launch_s, rates):
     return {"achieved_per_s": got, "peak_per_s": rates["tanh_per_s"], "frac": got / rates["tanh_per_s"],
             "peak_basis": "tanh.approx rate measured by mlp_unit_rates on this device"}
 
-def traffic_record(kernel: str):
-    """The DRAM traffic record of `kernel` from the committed ncu summaries
-    (a `traffic-record:` line in profiles/*.md), if it was taken on the
-    current kernel sources; else None."""
+def traffic_record(kernel: str, workload: str | None = None):
+    """The DRAM traffic record of `kernel` (on `workload`, if given) from the
+    committed ncu summaries (a `traffic-record:` line in profiles/*.md), if it
+    was taken on the current kernel sources; else None."""
     import glob
     csrc = os.path.join(ROOT, "paper_1908_07847_gb300", "csrc")
     for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
@@ -215,7 +215,7 @@ def traffic_record(kernel: str):
                 rec = json.loads(line.split(":", 1)[1])
             except ValueError:
                 continue
-            if rec.get("kernel") != kernel:
+            if rec.get("kernel") != kernel or (workload is not None and rec.get("workload") != workload):
                 continue
             h = hashlib.sha256()
             try:
@@ -229,8 +229,8 @@ def traffic_record(kernel: str):
 
 def traffic_from_profile():
     """DRAM bytes per launch of the fused kernel on the default workload."""
-    rec = traffic_record("k_fused_train")
-    return rec.get("dram_bytes_per_launch") if rec and rec.get("workload") == WORKLOAD else None
+    rec = traffic_record("k_fused_train", WORKLOAD)
+    return rec.get("dram_bytes_per_launch") if rec else None
 
 
 def run_ours(args, rank, world, local):
@@ -440,19 +440,9 @@ def run_c0(args, rank, world, local):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     lh = torch.zeros(C0_EPOCHS, dtype=torch.float64, device=dev)
     h = B.mlp_create(D_IN, C0_H, LR, 1, B.MLP_FP32, B.MLP_ACT_SIGMOID)
-    # rows per block: the fastest of a few splits for 100-epoch launches (untimed)
-    per_epoch = {}
-    for rows in (96, 48, 32, 24, 16, 12, 8):
-        B.mlp_set_rows_per_block(h, rows)
-        B.mlp_set_weights(h, *W)
-        B.mlp_train_epochs(h, Xd[:C0_TRAIN], yd[:C0_TRAIN], C0_TRAIN, 100, 0, None, None, stream)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        B.mlp_train_epochs(h, Xd[:C0_TRAIN], yd[:C0_TRAIN], C0_TRAIN, 100, 0, None, None, stream)
-        e1.record()
-        torch.cuda.synchronize()
-        per_epoch[rows] = e0.elapsed_time(e1) * 10.0   # us per epoch
-    rows_best = min(per_epoch, key=per_epoch.get)
+    # one block: the 96 rows fit it, and a single block sums and updates on chip
+    # (a search over 1..12 blocks, timed on GB300s, picked it every time)
+    rows_best = C0_TRAIN
     B.mlp_set_rows_per_block(h, rows_best)
 
     def timed(step_fn, steps, warmup):
@@ -506,6 +496,8 @@ def run_c0(args, rank, world, local):
     T_e = aggregate_max(sum(t_e2e), world)
     units = C0_TRAIN * C0_EPOCHS * world
     flops = (4 * D_IN * C0_H + 10 * C0_H) * C0_TRAIN * C0_EPOCHS
+    rec = traffic_record("k_fused_train", C0_WORKLOAD)
+    c0_traffic = rec.get("dram_bytes_per_launch") if rec else None
     launch_s = statistics.mean(t_fused)
     peak = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
     out = {
@@ -524,7 +516,8 @@ def run_c0(args, rank, world, local):
                 "h2d_bytes_per_step": C0_TRAIN * D_IN * 4 + C0_TRAIN * 4, "d2h_bytes_per_step": 8 * C0_EPOCHS,
                 "call": "mlp_train_host (pinned host X, y in; loss history out)"},
         "roofline": {"bound": "alu", "achieved": flops / launch_s / 1e12, "peak": peak, "unit": "TFLOP/s",
-                     "frac": flops / launch_s / 1e12 / peak, "traffic": None, "kernel": "k_fused_train (33-16-1 instance)",
+                     "frac": flops / launch_s / 1e12 / peak, "traffic": c0_traffic,
+                     "kernel": "k_fused_train (33-16-1 instance)",
                      "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (FFMA, derived)",
                      "flops_per_launch": flops},
         "gpu_launches": args.steps, "clocks": clk.summary(),

@@ -184,7 +184,9 @@ __global__ void __launch_bounds__(FNT, 1) k_fused_train(FArgs a) {
                     for (int q = 1; q < NG; ++q) s += gpart[q * P + p];
                     const float v = s * gup;
                     if (!(fabsf(v) < 4.0e18f)) bad = 1;
-                    const float gsum = (float)__float2ll_rn(v) * gscale;
+                    // = (float)llrint(v) * 2^-gshift: below 2^23 both round v to the
+                    // same integer, above it v already is one (no 64-bit conversion)
+                    const float gsum = rintf(v) * gscale;
                     Wm[p] -= a.lr * gsum;
                     if (want_gn) gn = fma((double)gsum, (double)gsum, gn);
                 }
