@@ -45,3 +45,28 @@ def test_aggregate_max_over_two_gloo_ranks():
 def test_single_rank_identity():
     import bench
     assert bench.aggregate_max(3.25, 1) == 3.25
+
+
+def test_traffic_records_follow_kernel_sources(tmp_path, monkeypatch):
+    """The roofline's DRAM traffic comes from committed ncu summaries only while
+    the kernel's sources still hash to the recorded value, and a record is
+    picked by kernel and workload."""
+    import shutil
+
+    import bench
+    assert bench.traffic_from_profile() is not None
+    c0 = bench.traffic_record("k_fused_train", bench.C0_WORKLOAD)
+    c1 = bench.traffic_record("k_fused_train", bench.WORKLOAD)
+    assert c0 is not None and c1 is not None and c0 != c1
+    assert bench.traffic_record("k_fused_train", "no such workload") is None
+    # a copy of the tree whose fused kernel source differs by one byte
+    root = tmp_path / "tree"
+    shutil.copytree(os.path.join(bench.ROOT, "profiles"), root / "profiles")
+    csrc = root / "paper_1908_07847_gb300" / "csrc"
+    shutil.copytree(os.path.join(bench.ROOT, "paper_1908_07847_gb300", "csrc"), csrc)
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    assert bench.traffic_record("k_fused_train", bench.WORKLOAD) is not None
+    with open(csrc / "fused_kernels.cu", "a") as f:
+        f.write("\n")
+    assert bench.traffic_record("k_fused_train", bench.WORKLOAD) is None
+    assert bench.traffic_record("k_batched_train") is not None
