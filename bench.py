@@ -636,6 +636,7 @@ def run_c2(args, rank, world, local):
                    "l2": "flushed between timed steps (256 MiB write, outside the timed intervals)"},
         "roofline": {"bound": "alu", "achieved": flops / launch_s / 1e12, "peak": peak, "unit": "TFLOP/s",
                      "frac": flops / launch_s / 1e12 / peak, "traffic": c2_traffic, "kernel": "k_batched_train<36,sigmoid>",
+                     "peak_basis": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (FFMA, derived)",
                      "flops_per_launch": flops},
         "plain_fp32": {"value": plain, "unit": "sample-steps/s",
                        "path": "mlp_step_plain on one mid-size net of the workload (the plain path takes one net "
