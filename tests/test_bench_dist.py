@@ -70,3 +70,27 @@ def test_traffic_records_follow_kernel_sources(tmp_path, monkeypatch):
         f.write("\n")
     assert bench.traffic_record("k_fused_train", bench.WORKLOAD) is None
     assert bench.traffic_record("k_batched_train") is not None
+
+
+def test_reference_arm_prints_one_contract_line():
+    """`bench.py --impl reference` (the FP64 oracle on the host cores) runs
+    without a GPU and prints one JSON line with the keys the benchmark
+    contract asks of the reference arm."""
+    import json
+    import subprocess
+    import sys
+
+    import bench
+    out = subprocess.run([sys.executable, os.path.join(bench.ROOT, "bench.py"), "--impl", "reference", "--steps", "2",
+                          "--warmup", "1"], capture_output=True, text=True, timeout=600, cwd=bench.ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == "sample-steps/s"
+    assert d["value"] > 0 and d["steps"] == 2 and d["warmup"] == 1 and d["higher_is_better"] is True
+    assert d["gpu_launches"] == 0 and d["n_gpus"] == 1
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
+    assert d["config"]["workload"] == bench.WORKLOAD
