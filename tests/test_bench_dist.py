@@ -94,3 +94,23 @@ def test_reference_arm_prints_one_contract_line():
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
     assert d["config"]["workload"] == bench.WORKLOAD
+
+
+def test_reference_arm_under_torchrun_prints_once():
+    """Launched the way the multi-GPU runs launch it (torchrun, two ranks),
+    the reference arm runs on rank 0 only and prints one line; the other rank
+    exits 0 without work."""
+    import json
+    import subprocess
+    import sys
+
+    import bench
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2", "--master-addr",
+           "127.0.0.1", "--master-port", str(_free_port()), os.path.join(bench.ROOT, "bench.py"), "--impl",
+           "reference", "--gpus", "2", "--steps", "1", "--warmup", "1"]
+    out = subprocess.run(cmd, capture_output=True, text=True, timeout=600, cwd=bench.ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [ln for ln in out.stdout.splitlines() if ln.strip().startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 2
