@@ -145,10 +145,10 @@ mlp_status mlp_train_epochs(mlp_t net, const void *X, const void *y, int64_t n,
 
 /* mlp_train_epochs on host buffers: copies X and y to device staging memory
  * owned by the handle, trains, and copies the loss history back to
- * loss_hist_host (may be NULL).  Synchronous.  A one-epoch call on an FP32 or
- * FP64 handle whose buffers are all page-locked (cudaHostAlloc, pinned tensors)
- * skips the staging: the kernels read X and y through the device's mapping of
- * that memory and write the loss there. */
+ * loss_hist_host (may be NULL).  Synchronous.  A one-epoch call that takes the
+ * fused FP32 kernel (D <= 64, H <= 128), with all buffers page-locked
+ * (cudaHostAlloc, pinned tensors), skips the staging: the kernel reads X and y
+ * through the device's mapping of that memory and writes the loss there. */
 mlp_status mlp_train_host(mlp_t net, const void *X_host, const void *y_host,
                           int64_t n, int32_t epochs, int64_t minibatch,
                           double *loss_hist_host, void *stream);

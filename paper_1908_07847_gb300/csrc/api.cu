@@ -384,12 +384,13 @@ mlp_status mlp_train_host(mlp_t h, const void *X_host, const void *y_host, int64
         return fail(MLP_EINVAL, "mlp_train_host: bad arguments");
     DeviceScope ds(h->device);
     cudaStream_t st = (cudaStream_t)stream;
-    if (epochs == 1 && n > 0 && h->cfg.prec != MLP_BF16) {
-        // One epoch reads every row once: page-locked host buffers are read where
-        // they are, through the device's mapping of them (over NVLink-C2C on a
-        // Grace-Blackwell node), and the loss is written straight back, instead
-        // of staging copies that only add their latency.  The bf16 paths load
-        // X by TMA from device memory and always stage.
+    if (epochs == 1 && n > 0 && h->cfg.prec == MLP_FP32 && mlp::fused_supported(h->cfg.D, h->cfg.H)) {
+        // One epoch of the fused kernel reads every row once: page-locked host
+        // buffers are read where they are, through the device's mapping of them
+        // (over NVLink-C2C on a Grace-Blackwell node), and the loss is written
+        // straight back, instead of staging copies that only add their latency.
+        // The plain path reads X once per tile of hidden units and the bf16 paths
+        // load it by TMA from device memory: those always stage.
         const void *Xm = mapped_host(X_host), *ym = mapped_host(y_host);
         double *lm = loss_hist_host ? (double *)mapped_host(loss_hist_host) : nullptr;
         if (Xm && ym && (!loss_hist_host || lm)) {
