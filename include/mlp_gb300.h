@@ -134,7 +134,8 @@ mlp_status mlp_step_plain(mlp_t net, const void *X, const void *y, int64_t n,
  *     2048, gnorm_hist NULL: one tensor-core (tcgen05) kernel per call, blocks
  *     in clusters of H/256 that share z2 through distributed shared memory,
  *     bf16 operands (W1, h and the hidden deltas rounded to bf16, FP32
- *     accumulation and FP32 master weights); X must be 16-byte aligned;
+ *     accumulation and FP32 master weights); X must be 16-byte aligned,
+ *     n < 2^31 - 127 and epochs x ceil(n / 128) < 2^31 (else MLP_EINVAL);
  *   everything else: the plain path, one step at a time (FP32 arithmetic on
  *     bf16 inputs for MLP_BF16).
  * The tensor-core kernel records MLP_ECUDA through mlp_check if it ever finds
@@ -207,7 +208,9 @@ mlp_status mlp_set_rows_per_block(mlp_t net, int32_t rows);
  * (rows beyond 256 are streamed from device memory each epoch).  MLP_BF16
  * (bf16 X, 16-byte aligned, padding columns zero; FP32 master weights,
  * tcgen05 tensor cores, one block per net): sigmoid only, D % 8 == 0,
- * 8 <= D <= 56, H = 128 or 256.
+ * 8 <= D <= 56, H = 128 or 256, n < 2^31 - 127 per net, and in one
+ * mlp_batch_run epochs x ceil(n / 128) < 2^31 for the largest net (MLP_EINVAL
+ * otherwise).
  */
 typedef struct {
     int32_t H;

@@ -79,6 +79,13 @@ struct DeviceScope {
     }
 };
 
+// The tensor-core kernels address rows with 32-bit TMA coordinates and count a
+// launch's tiles (and derive their barrier phases) in 32-bit integers.
+bool tc_fits_32bit(int64_t n, int64_t epochs) {
+    const int64_t tiles = (n + 127) / 128;
+    return n <= (int64_t)INT32_MAX - 127 && epochs * tiles <= (int64_t)INT32_MAX;
+}
+
 // The device address of page-locked host memory, or NULL for pageable memory.
 const void *mapped_host(const void *p) {
     cudaPointerAttributes a;
@@ -342,6 +349,8 @@ mlp_status mlp_train_epochs(mlp_t h, const void *X, const void *y, int64_t n, in
         return MLP_OK;
     }
     if (h->cfg.prec == MLP_BF16 && h->cfg.act == MLP_ACT_SIGMOID && !gnorm_hist && mlp::tc_cluster_supported(D, H)) {
+        if (!tc_fits_32bit(n, epochs))
+            return fail(MLP_EINVAL, "mlp_train_epochs: more than 2^31 - 128 rows, or epochs x tiles beyond 2^31");
         void *before = h->fs;
         mlp_status s = grow(&h->fs, &h->fs_cap, mlp::tc_cluster_scratch_bytes(D, H), "cluster scratch");
         if (s) return s;
@@ -534,6 +543,7 @@ struct mlp_batch {
     void *tc_descs;
     int *order;
     int *status;
+    int64_t max_tiles;         // BF16: the most 128-row tiles of any net
 };
 
 // BF16 plan: per-net TMA tensor maps and descriptors for the tcgen05 kernel.
@@ -549,6 +559,7 @@ static mlp_status batch_create_tc(int32_t act, int32_t D, const mlp_net_desc *ne
         if (d.n < 0 || !d.params || (d.n > 0 && (!d.X || !d.y)))
             return fail(MLP_EINVAL, "mlp_batch_create: net %d has a null buffer or n < 0", t);
         if (((uintptr_t)d.X & 15) != 0) return fail(MLP_EINVAL, "mlp_batch_create: net %d X not 16-byte aligned", t);
+        if (!tc_fits_32bit(d.n, 1)) return fail(MLP_EINVAL, "mlp_batch_create: net %d has more than 2^31 - 128 rows", t);
         cost[t] = (double)d.n * d.H;
     }
     std::vector<int> order(n_nets);
@@ -568,6 +579,8 @@ static mlp_status batch_create_tc(int32_t act, int32_t D, const mlp_net_desc *ne
     b->lr = lr;
     b->loss_mean = loss_mean ? 1 : 0;
     b->nets = nullptr;
+    b->max_tiles = 0;
+    for (int t = 0; t < n_nets; ++t) b->max_tiles = std::max<int64_t>(b->max_tiles, (nets[t].n + 127) / 128);
     const size_t N1 = (size_t)(n_nets > 0 ? n_nets : 1);
     const size_t mb = (mlp::tc_tmap_bytes() + 127) & ~(size_t)127;
     const size_t db = (mlp::tc_desc_bytes() + 15) & ~(size_t)15;
@@ -684,6 +697,8 @@ mlp_status mlp_batch_run(mlp_batch_t b, int32_t epochs, void *stream) {
     if (epochs < 0) return fail(MLP_EINVAL, "mlp_batch_run: epochs < 0");
     DeviceScope ds(b->device);
     if (b->prec == MLP_BF16) {
+        if ((int64_t)epochs * b->max_tiles > (int64_t)INT32_MAX)
+            return fail(MLP_EINVAL, "mlp_batch_run: epochs x tiles of the largest net beyond 2^31; split the epochs");
         CK(mlp::tc_batched_train(b->tc_descs, b->order, b->n_nets, b->D, epochs, b->lr, b->loss_mean, b->status,
                                  (cudaStream_t)stream),
            "tensor-core batched training kernel");
