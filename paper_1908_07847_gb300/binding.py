@@ -111,14 +111,20 @@ def _ck(status):
 
 
 def _p(x):
-    """Device/host address of a torch tensor, numpy array, int or None."""
+    """Device/host address of a torch tensor, numpy array, int or None.  The
+    library reads and writes dense row-major buffers, so a tensor or array
+    view that is not C-contiguous is refused rather than misread."""
     if x is None:
         return None
     if isinstance(x, int):
         return x
     if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor is not contiguous (call .contiguous() first)")
         return x.data_ptr()
     if hasattr(x, "ctypes"):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array is not C-contiguous (use numpy.ascontiguousarray)")
         return x.ctypes.data
     raise TypeError("cannot take the address of %r" % type(x))
 

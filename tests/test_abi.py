@@ -41,3 +41,22 @@ def test_host_side_validation_without_gpu(built):
     with pytest.raises(B.MLPError):
         B.mlp_workspace_bytes(B.MLP_FP32, 0, 64, 10)
     assert "mlp_workspace_bytes" in B.mlp_last_error()
+
+
+def test_binding_refuses_non_contiguous_buffers():
+    """The binding passes raw addresses: a strided view would be read as if it
+    were dense, so it is refused; dense arrays, tensors, ints and None pass."""
+    import numpy as np
+    import torch
+    a = np.zeros((4, 6), np.float32)
+    assert B._p(a) == a.ctypes.data
+    assert B._p(a[1:3]) == a[1:3].ctypes.data          # a row slice stays dense
+    with pytest.raises(ValueError):
+        B._p(a[:, :3])
+    with pytest.raises(ValueError):
+        B._p(a.T)
+    t = torch.zeros(4, 6)
+    assert B._p(t) == t.data_ptr()
+    with pytest.raises(ValueError):
+        B._p(t.t())
+    assert B._p(None) is None and B._p(1234) == 1234
