@@ -130,12 +130,15 @@ mlp_status mlp_step_plain(mlp_t net, const void *X, const void *y, int64_t n,
  * update's gradient.  Paths, by precision and shape:
  *   MLP_FP32, D <= 64, H <= 128: one fused cooperative kernel per call
  *     (forward, backward, cross-block reduction and update per step);
- *   MLP_BF16, sigmoid, D % 8 == 0, 8 <= D <= 48, H a multiple of 256 up to
- *     2048, gnorm_hist NULL: one tensor-core (tcgen05) kernel per call, blocks
+ *   MLP_BF16 (sigmoid or tanh), D % 8 == 0, 8 <= D <= 48, H a multiple of
+ *     256 up to 2048: one tensor-core (tcgen05) kernel per call, blocks
  *     in clusters of H/256 that share z2 through distributed shared memory,
  *     bf16 operands (W1, h and the hidden deltas rounded to bf16, FP32
  *     accumulation and FP32 master weights); X must be 16-byte aligned,
  *     n < 2^31 - 127 and epochs x ceil(n / 128) < 2^31 (else MLP_EINVAL);
+ *     the gradient norm, if asked for, is taken from the summed FP32 gradient
+ *     in FP64 by a second small kernel; a device that refuses the cooperative
+ *     cluster launch gives MLP_EUNSUPPORTED;
  *   everything else: the plain path, one step at a time (FP32 arithmetic on
  *     bf16 inputs for MLP_BF16).
  * The tensor-core kernel records MLP_ECUDA through mlp_check if it ever finds
@@ -202,12 +205,15 @@ mlp_status mlp_set_rows_per_block(mlp_t net, int32_t rows);
  * its own H and n).  All nets share D, the activation, lr, the loss scaling and
  * full-batch gradient descent (Sec. 2.2).  Each descriptor names device memory:
  * X (n x D row-major, float), y (n floats), params (the net's packed weights
- * [W1 (H x D), b1, w2, b2], float, trained in place) and loss_hist (epochs
- * doubles, may be NULL; receives the loss before each epoch's update).
+ * [W1 (H x D), b1, w2, b2], float, trained in place), loss_hist (epochs
+ * doubles, may be NULL; receives the loss before each epoch's update) and
+ * gnorm_hist (epochs doubles, may be NULL; receives the 2-norm of the gradient
+ * each epoch's update applied, summed in FP64 in a fixed order: the convergence
+ * check beside the loss).
  * Limits of this build: MLP_FP32 (FP32 X): D <= 64, H <= 128; n is unbounded
  * (rows beyond 256 are streamed from device memory each epoch).  MLP_BF16
  * (bf16 X, 16-byte aligned, padding columns zero; FP32 master weights,
- * tcgen05 tensor cores, one block per net): sigmoid only, D % 8 == 0,
+ * tcgen05 tensor cores, one block per net): sigmoid or tanh, D % 8 == 0,
  * 8 <= D <= 56, H = 128 or 256, n < 2^31 - 127 per net, and in one
  * mlp_batch_run epochs x ceil(n / 128) < 2^31 for the largest net (MLP_EINVAL
  * otherwise).
@@ -219,6 +225,7 @@ typedef struct {
     const float *y;
     float *params;
     double *loss_hist;
+    double *gnorm_hist;
 } mlp_net_desc;
 
 typedef struct mlp_batch *mlp_batch_t;
@@ -239,6 +246,20 @@ mlp_status mlp_batch_run(mlp_batch_t b, int32_t epochs, void *stream);
  * (MLP_OK or MLP_ENONFINITE). */
 mlp_status mlp_batch_check(mlp_batch_t b, void *stream);
 
+/* Kernel shape of an FP32 plan's launches, a tuning knob (autotune.py times
+ * the shapes a plan allows and keeps the fastest).  Every shape runs the same
+ * method and meets the same FP32 bars against the oracle; a given shape is
+ * bitwise reproducible, two shapes differ by the order of their FP32 sums.
+ *   0  one hidden unit a lane, blocks of 8 warps, two per SM (any D <= 64);
+ *   1  two hidden units a lane (each row word read from shared memory feeds
+ *      two multiply-adds), blocks of 4 warps, two per SM, one row in flight
+ *      per lane (D <= 36);
+ *   2  as 1 with two rows in flight per lane (D = 33, the paper's markers).
+ * A new FP32 plan has shape 0.  set: MLP_EINVAL for a shape the plan's D
+ * does not take, MLP_EUNSUPPORTED for a BF16 plan.  get: -1 for BF16 plans. */
+mlp_status mlp_batch_set_shape(mlp_batch_t b, int32_t shape);
+mlp_status mlp_batch_get_shape(mlp_batch_t b, int32_t *shape);
+
 /* Free the plan (not the buffers its descriptors name).  NULL is ignored. */
 void mlp_batch_destroy(mlp_batch_t b);
 
@@ -250,12 +271,40 @@ mlp_status mlp_batch_train(int32_t prec, int32_t act, int32_t D,
                            void *stream);
 
 /*
+ * Many-nets training on host buffers: the end-to-end form of mlp_batch_run,
+ * for callers whose data live in host memory.  mlp_batch_create_host makes a
+ * plan that owns device memory for every net's rows, labels, weights and
+ * histories, laid out as on the host: all nets' rows one net after another
+ * (net t's n[t] x D rows follow net t-1's), their labels likewise, the packed
+ * weights [W1, b1, w2, b2] of (D + 2) H[t] + 1 floats one net after another,
+ * and n_nets x max_epochs doubles of loss history.  H and n are host arrays of
+ * n_nets entries; the limits are mlp_batch_create's.  Every
+ * mlp_batch_run_host call then copies X_host (float for MLP_FP32, bfloat16
+ * bits for MLP_BF16), y_host and params_in_host to the device, trains
+ * `epochs` (<= max_epochs) epochs in one launch, and copies the trained
+ * weights to params_out_host (may equal params_in_host) and, if
+ * loss_hist_host is not NULL, the losses to it as n_nets x epochs doubles.
+ * Synchronous; returns the plan's status as mlp_batch_check does.  Page-locked
+ * host buffers make the copies asynchronous DMA; pageable ones work, slower.
+ * mlp_batch_run_host on a plan from mlp_batch_create returns MLP_EINVAL.
+ */
+mlp_status mlp_batch_create_host(int32_t prec, int32_t act, int32_t D,
+                                 const int32_t *H, const int64_t *n,
+                                 int32_t n_nets, int32_t max_epochs, float lr,
+                                 int32_t loss_mean, mlp_batch_t *out);
+mlp_status mlp_batch_run_host(mlp_batch_t b, const void *X_host,
+                              const float *y_host, const float *params_in_host,
+                              float *params_out_host, double *loss_hist_host,
+                              int32_t epochs, void *stream);
+
+/*
  * Fused training (as mlp_train_epochs, without the gradient norm) on
  * caller-owned weights, allocating no device memory.  It is for callers that
- * cannot call cudaMalloc: code that runs while a stream is being captured into
- * a CUDA graph, a framework that hands out every byte of device memory from
- * its own pool, or a real-time loop that must not block on the allocator.  The
- * paper has no counterpart; it is a property of this library's interface.
+ * cannot call cudaMalloc: a framework that hands out every byte of device
+ * memory from its own pool (an allocation beside the pool fails or fragments
+ * it), or a real-time loop that must not block on the allocator, whose
+ * cudaMalloc and cudaFree synchronise the device.  The paper has no
+ * counterpart; it is a property of this library's interface.
  *
  * The kernel's scratch (fixed-point gradient accumulators, a barrier counter
  * and a status word) lives in one statically sized device array of 203,520
@@ -263,9 +312,13 @@ mlp_status mlp_batch_train(int32_t prec, int32_t act, int32_t D,
  * Hence the limits D <= 64 and H <= 128; larger networks are rejected with
  * MLP_EINVAL.  Every call uses that one array and clears it on `stream` before
  * its kernel runs, so calls that overlap on the GPU (from two streams or two
- * threads) race with each other and must be ordered by the caller.  The first
- * call on a device also looks up the array's device address (and may load the
- * library's device code); make that first call before any stream capture.
+ * threads) race with each other and must be ordered by the caller.  Every
+ * call looks up the array's device address with the device current (no
+ * allocation; the address can change after cudaDeviceReset).  The first call
+ * on a device, and the first call with each new combination of activation,
+ * input-width class (D up to 8, 16, 36, 48, 64) and hidden-width class (H up
+ * to 32, 64, 128), may load that kernel's device code and set its
+ * shared-memory attribute; make those first calls before any stream capture.
  *
  * X (n x D), y (n), params (packed [W1, b1, w2, b2], 16-byte aligned, trained
  * in place) and loss_hist (epochs doubles, may be NULL) are device memory.

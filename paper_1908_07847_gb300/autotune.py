@@ -1,11 +1,17 @@
-"""Autotuner for the fused training kernel's tile shape (rows per block).
+"""Autotuners for the training kernels' tile shapes.
 
-The fused kernel splits each step's rows over blocks; more blocks shorten the
-row phase but add cross-block traffic and barrier participants.  ``tune_fused``
-times one-epoch launches for each candidate on the caller's device and shape and
-caches the fastest in a JSON file (``$MLP_GB300_TUNE_CACHE``, else
-``~/.cache/mlp_gb300/tune.json``), keyed by device name and shape.  Timing uses
-CUDA events on the launching stream; the library does the work.
+* ``tune_fused``: rows per block of the fused single-network kernel.  It splits
+  each step's rows over blocks; more blocks shorten the row phase but add
+  cross-block traffic and barrier participants.
+* ``tune_batched``: the kernel shape of an FP32 many-nets plan
+  (mlp_batch_set_shape): one hidden unit a lane in blocks of 8 warps, or two
+  units a lane in blocks of 4 warps with one or two rows in flight.  Which is
+  fastest depends on the plan's mix of widths and row counts.
+
+Each times its candidates on the caller's device and workload and caches the
+fastest in a JSON file (``$MLP_GB300_TUNE_CACHE``, else
+``~/.cache/mlp_gb300/tune.json``), keyed by device name and workload.  Timing
+uses CUDA events on the launching stream; the library does the work.
 """
 from __future__ import annotations
 
@@ -95,3 +101,69 @@ def configure(handle, X, y, D, H, n, minibatch=0, act=B.MLP_ACT_SIGMOID):
     rows, _ = tune_fused(X, y, D, H, n, minibatch, act)
     B.mlp_set_rows_per_block(handle, rows)
     return rows
+
+
+BATCH_SHAPES = (0, 1, 2)
+
+
+def _batch_key(device_name, D, Hs, ns, act):
+    import numpy as np
+    Hs = np.asarray(Hs, np.int64)
+    ns = np.asarray(ns, np.int64)
+    return "%s|batched|D=%d|nets=%d|rows=%d|work=%d|act=%d" % (device_name, D, len(Hs), int(ns.sum()),
+                                                              int((Hs * ns).sum()), act)
+
+
+def tune_batched(plan, D, Hs, ns, params, act=B.MLP_ACT_SIGMOID, epochs=25, reps=3, shapes=BATCH_SHAPES,
+                 use_cache=True):
+    """Best kernel shape for an FP32 many-nets plan; sets it on the plan.
+
+    plan: from mlp_batch_create; Hs, ns: its nets' widths and row counts (the
+    cache key); params: the device tensor(s) holding the nets' packed weights,
+    which the timed launches train and which are restored afterwards.  Each
+    shape the plan's D takes is timed on `epochs`-epoch launches of the plan
+    itself.  Returns (shape, {shape: milliseconds per epoch})."""
+    import torch
+    dev_name = torch.cuda.get_device_name()
+    key = _batch_key(dev_name, D, Hs, ns, act)
+    with _lock:
+        table = _load() if use_cache else {}
+        if key in table:
+            best = int(table[key]["shape"])
+            B.mlp_batch_set_shape(plan, best)
+            return best, {int(k): v for k, v in table[key]["ms_per_epoch"].items()}
+    stream = torch.cuda.current_stream().cuda_stream
+    params = params if isinstance(params, (list, tuple)) else [params]
+    saved = [p.clone() for p in params]
+    before = B.mlp_batch_get_shape(plan)
+    times = {}
+    try:
+        for shape in shapes:
+            try:
+                B.mlp_batch_set_shape(plan, int(shape))
+            except B.MLPError:
+                continue          # not available for this D
+            B.mlp_batch_run(plan, epochs, stream)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                B.mlp_batch_run(plan, epochs, stream)
+            e1.record()
+            torch.cuda.synchronize()
+            times[int(shape)] = e0.elapsed_time(e1) / (reps * epochs)
+        if B.mlp_batch_check(plan, stream) != B.MLP_OK:
+            raise B.MLPError(B.MLP_ECUDA, "autotune run failed: " + B.mlp_last_error())
+    finally:
+        for p, q in zip(params, saved):
+            p.copy_(q)
+        torch.cuda.synchronize()
+        B.mlp_batch_set_shape(plan, before)
+    best = min(times, key=times.get)
+    B.mlp_batch_set_shape(plan, best)
+    with _lock:
+        table = _load() if use_cache else {}
+        table[key] = {"shape": best, "ms_per_epoch": {str(k): v for k, v in times.items()}}
+        if use_cache:
+            _store(table)
+    return best, times

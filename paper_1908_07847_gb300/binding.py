@@ -25,7 +25,8 @@ EXPORTS = [
     "mlp_forward", "mlp_backward", "mlp_update", "mlp_step_plain", "mlp_train_epochs",
     "mlp_train_host", "mlp_predict", "mlp_check", "mlp_workspace_bytes", "mlp_forward_w",
     "mlp_backward_w", "mlp_debug_skip_block", "mlp_set_rows_per_block", "mlp_batch_train",
-    "mlp_batch_create", "mlp_batch_run", "mlp_batch_check", "mlp_batch_destroy", "mlp_train_fused_noalloc",
+    "mlp_batch_create", "mlp_batch_run", "mlp_batch_check", "mlp_batch_destroy", "mlp_batch_create_host",
+    "mlp_batch_run_host", "mlp_batch_set_shape", "mlp_batch_get_shape", "mlp_train_fused_noalloc",
     "mlp_zscore_workspace_bytes", "mlp_zscore", "mlp_unit_rates", "mlp_last_error", "mlp_version",
 ]
 
@@ -43,7 +44,8 @@ class mlp_config(ctypes.Structure):
 
 class mlp_net_desc(ctypes.Structure):
     _fields_ = [("H", ctypes.c_int32), ("n", ctypes.c_int64), ("X", ctypes.c_void_p),
-                ("y", ctypes.c_void_p), ("params", ctypes.c_void_p), ("loss_hist", ctypes.c_void_p)]
+                ("y", ctypes.c_void_p), ("params", ctypes.c_void_p), ("loss_hist", ctypes.c_void_p),
+                ("gnorm_hist", ctypes.c_void_p)]
 
 
 _lib = None
@@ -89,6 +91,10 @@ def lib():
             "mlp_batch_run": (S, [V, I32, V]),
             "mlp_batch_check": (S, [V, V]),
             "mlp_batch_destroy": (None, [V]),
+            "mlp_batch_create_host": (S, [I32, I32, I32, V, V, I32, I32, F, I32, ctypes.POINTER(V)]),
+            "mlp_batch_run_host": (S, [V, V, V, V, V, V, I32, V]),
+            "mlp_batch_set_shape": (S, [V, I32]),
+            "mlp_batch_get_shape": (S, [V, ctypes.POINTER(I32)]),
             "mlp_train_fused_noalloc": (S, [I32, I32, I32, I64, V, V, V, F, I32, I32, I64, V, V, V]),
             "mlp_last_error": (ctypes.c_char_p, []),
             "mlp_version": (ctypes.c_char_p, []),
@@ -239,6 +245,34 @@ def mlp_batch_check(b, stream=0):
 
 def mlp_batch_destroy(b):
     lib().mlp_batch_destroy(b)
+
+
+def mlp_batch_set_shape(b, shape):
+    return _ck(lib().mlp_batch_set_shape(b, shape))
+
+
+def mlp_batch_get_shape(b):
+    v = ctypes.c_int32()
+    _ck(lib().mlp_batch_get_shape(b, ctypes.byref(v)))
+    return v.value
+
+
+def mlp_batch_create_host(prec, act, D, Hs, ns, max_epochs, lr, loss_mean=1):
+    """Plan owning device copies of every net's data (host layout: nets one
+    after another); Hs and ns are sequences of ints."""
+    import numpy as np
+    H = np.ascontiguousarray(np.asarray(Hs, np.int32))
+    n = np.ascontiguousarray(np.asarray(ns, np.int64))
+    if H.shape != n.shape:
+        raise ValueError("Hs and ns differ in length")
+    b = ctypes.c_void_p()
+    _ck(lib().mlp_batch_create_host(prec, act, D, _p(H), _p(n), len(H), max_epochs, lr, loss_mean, ctypes.byref(b)))
+    return b.value
+
+
+def mlp_batch_run_host(b, X_host, y_host, params_in_host, params_out_host, loss_hist_host, epochs, stream=0):
+    return _ck(lib().mlp_batch_run_host(b, _p(X_host), _p(y_host), _p(params_in_host), _p(params_out_host),
+                                        _p(loss_hist_host), epochs, stream))
 
 
 def mlp_train_fused_noalloc(act, D, H, n, X, y, params, lr, loss_mean, epochs, minibatch=0, loss_hist=None,

@@ -33,6 +33,8 @@ struct mlp_net {
     size_t xstage_cap = 0, ystage_cap = 0;
     double *lstage = nullptr;
     size_t lstage_cap = 0;
+    double *gnp = nullptr;    // per-epoch gradient-norm partials (tensor-core cluster path)
+    size_t gnp_cap = 0;
     int skip_block = -1;
     int rows_per_block = 32;
     int max_clusters = 1 << 30;   // cap on clusters of the tensor-core kernel
@@ -234,6 +236,7 @@ void mlp_destroy(mlp_t h) {
     if (h->xstage) cudaFree(h->xstage);
     if (h->ystage) cudaFree(h->ystage);
     if (h->lstage) cudaFree(h->lstage);
+    if (h->gnp) cudaFree(h->gnp);
     delete h;
 }
 
@@ -348,7 +351,7 @@ mlp_status mlp_train_epochs(mlp_t h, const void *X, const void *y, int64_t n, in
            "fused training kernel");
         return MLP_OK;
     }
-    if (h->cfg.prec == MLP_BF16 && h->cfg.act == MLP_ACT_SIGMOID && !gnorm_hist && mlp::tc_cluster_supported(D, H)) {
+    if (h->cfg.prec == MLP_BF16 && mlp::tc_cluster_supported(D, H)) {
         if (!tc_fits_32bit(n, epochs))
             return fail(MLP_EINVAL, "mlp_train_epochs: more than 2^31 - 128 rows, or epochs x tiles beyond 2^31");
         void *before = h->fs;
@@ -358,9 +361,19 @@ mlp_status mlp_train_epochs(mlp_t h, const void *X, const void *y, int64_t n, in
             CK(cudaMemsetAsync(h->fs, 0, h->fs_cap, st), "cluster scratch reset");
             h->ctr = mlp::FusedCounters();
         }
-        CK(mlp::tc_cluster_train(X, (const float *)y, (float *)h->params, D, H, n, epochs, minibatch, h->cfg.lr,
-                                 h->cfg.loss_mean, loss_hist, h->status, h->fs, h->max_clusters, &h->ctr, st),
-           "tensor-core cluster kernel");
+        if (gnorm_hist) {
+            s = grow((void **)&h->gnp, &h->gnp_cap, sizeof(double) * (size_t)(H / 256 + 1) * epochs, "norm scratch");
+            if (s) return s;
+        }
+        cudaError_t e = mlp::tc_cluster_train(X, (const float *)y, (float *)h->params, D, H, n, epochs, minibatch,
+                                              h->cfg.lr, h->cfg.loss_mean, h->cfg.act, loss_hist, gnorm_hist, h->gnp,
+                                              h->status, h->fs, h->max_clusters, &h->ctr, st);
+        if (e == cudaErrorCooperativeLaunchTooLarge || e == cudaErrorNotSupported) {
+            cudaGetLastError();
+            return fail(MLP_EUNSUPPORTED, "tensor-core cluster kernel: the device refused its cooperative cluster "
+                                          "launch (%s)", cudaGetErrorString(e));
+        }
+        CK(e, "tensor-core cluster kernel");
         return MLP_OK;
     }
     // Plain path, one step at a time.
@@ -544,12 +557,19 @@ struct mlp_batch {
     int *order;
     int *status;
     int64_t max_tiles;         // BF16: the most 128-row tiles of any net
+    // mlp_batch_create_host: device copies of every net's data, host layout
+    void *owned = nullptr;
+    char *xd = nullptr;
+    float *yd = nullptr, *pd = nullptr;
+    double *ld = nullptr;
+    size_t x_bytes = 0, y_bytes = 0, p_bytes = 0;
+    int max_epochs = 0;
+    int shape = mlp::BATCH_SHAPE_U1;   // FP32 kernel shape (mlp_batch_set_shape)
 };
 
 // BF16 plan: per-net TMA tensor maps and descriptors for the tcgen05 kernel.
 static mlp_status batch_create_tc(int32_t act, int32_t D, const mlp_net_desc *nets, int32_t n_nets, float lr,
                                   int32_t loss_mean, mlp_batch_t *out) {
-    if (act != MLP_ACT_SIGMOID) return fail(MLP_EUNSUPPORTED, "mlp_batch_create: BF16 supports the sigmoid only");
     std::vector<double> cost(n_nets);
     for (int t = 0; t < n_nets; ++t) {
         const mlp_net_desc &d = nets[t];
@@ -583,7 +603,7 @@ static mlp_status batch_create_tc(int32_t act, int32_t D, const mlp_net_desc *ne
     for (int t = 0; t < n_nets; ++t) b->max_tiles = std::max<int64_t>(b->max_tiles, (nets[t].n + 127) / 128);
     const size_t N1 = (size_t)(n_nets > 0 ? n_nets : 1);
     const size_t mb = (mlp::tc_tmap_bytes() + 127) & ~(size_t)127;
-    const size_t db = (mlp::tc_desc_bytes() + 15) & ~(size_t)15;
+    const size_t db = mlp::tc_desc_bytes();   // the kernel reads them as an array: stride = sizeof
     const size_t maps = ((mb * N1) + 255) & ~(size_t)255;
     const size_t descs = ((db * N1) + 255) & ~(size_t)255;
     const size_t ords = ((sizeof(int) * N1) + 255) & ~(size_t)255;
@@ -605,7 +625,8 @@ static mlp_status batch_create_tc(int32_t act, int32_t D, const mlp_net_desc *ne
             delete b;
             return fail(MLP_ECUDA, "mlp_batch_create: tensor map of net %d: %s", t, cudaGetErrorString(e));
         }
-        mlp::tc_fill_desc(hdescs.data() + db * t, base + mb * t, d.y, d.params, d.loss_hist, d.n, d.H);
+        mlp::tc_fill_desc(hdescs.data() + db * t, base + mb * t, d.y, d.params, d.loss_hist, d.gnorm_hist, d.n,
+                          d.H);
     }
     cudaError_t e = cudaSuccess;
     if (n_nets > 0) {
@@ -644,7 +665,7 @@ mlp_status mlp_batch_create(int32_t prec, int32_t act, int32_t D, const mlp_net_
         if (d.n < 0 || !d.params || (d.n > 0 && (!d.X || !d.y)))
             return fail(MLP_EINVAL, "mlp_batch_create: net %d has a null buffer or n < 0", t);
         Hmax = d.H > Hmax ? d.H : Hmax;
-        host[t] = {(const float *)d.X, d.y, d.params, d.loss_hist, d.n, d.H, 0};
+        host[t] = {(const float *)d.X, d.y, d.params, d.loss_hist, d.gnorm_hist, d.n, d.H, 0};
         // lanes busy per row: a power-of-two segment up to 32, else 32 per 32 units
         int lanes = d.H <= 32 ? 4 : 32 * ((d.H + 31) / 32);
         while (d.H <= 32 && lanes < d.H) lanes <<= 1;
@@ -699,14 +720,29 @@ mlp_status mlp_batch_run(mlp_batch_t b, int32_t epochs, void *stream) {
     if (b->prec == MLP_BF16) {
         if ((int64_t)epochs * b->max_tiles > (int64_t)INT32_MAX)
             return fail(MLP_EINVAL, "mlp_batch_run: epochs x tiles of the largest net beyond 2^31; split the epochs");
-        CK(mlp::tc_batched_train(b->tc_descs, b->order, b->n_nets, b->D, epochs, b->lr, b->loss_mean, b->status,
-                                 (cudaStream_t)stream),
+        CK(mlp::tc_batched_train(b->tc_descs, b->order, b->n_nets, b->D, epochs, b->lr, b->loss_mean, b->act,
+                                 b->status, (cudaStream_t)stream),
            "tensor-core batched training kernel");
         return MLP_OK;
     }
     CK(mlp::batched_train(b->act, b->D, b->Hmax, b->nets, b->order, b->n_nets, epochs, b->lr, b->loss_mean,
-                          b->status, (cudaStream_t)stream),
+                          b->status, b->shape, (cudaStream_t)stream),
        "batched training kernel");
+    return MLP_OK;
+}
+
+mlp_status mlp_batch_set_shape(mlp_batch_t b, int32_t shape) {
+    if (!b) return fail(MLP_EINVAL, "mlp_batch_set_shape: null plan");
+    if (b->prec != MLP_FP32) return fail(MLP_EUNSUPPORTED, "mlp_batch_set_shape: FP32 plans only");
+    if (!mlp::batched_shape_supported(b->D, shape))
+        return fail(MLP_EINVAL, "mlp_batch_set_shape: shape %d does not take D = %d", shape, b->D);
+    b->shape = shape;
+    return MLP_OK;
+}
+
+mlp_status mlp_batch_get_shape(mlp_batch_t b, int32_t *shape) {
+    if (!b || !shape) return fail(MLP_EINVAL, "mlp_batch_get_shape: null argument");
+    *shape = b->prec == MLP_FP32 ? b->shape : -1;
     return MLP_OK;
 }
 
@@ -726,7 +762,90 @@ void mlp_batch_destroy(mlp_batch_t b) {
     if (!b) return;
     DeviceScope ds(b->device);
     cudaFree(b->mem);
+    if (b->owned) cudaFree(b->owned);
     delete b;
+}
+
+mlp_status mlp_batch_create_host(int32_t prec, int32_t act, int32_t D, const int32_t *H, const int64_t *n,
+                                 int32_t n_nets, int32_t max_epochs, float lr, int32_t loss_mean, mlp_batch_t *out) {
+    if (!out) return fail(MLP_EINVAL, "mlp_batch_create_host: null out");
+    *out = nullptr;
+    if (prec != MLP_FP32 && prec != MLP_BF16) return fail(MLP_EUNSUPPORTED, "mlp_batch_create_host: FP32 or BF16 only");
+    if (n_nets < 0 || (n_nets > 0 && (!H || !n)) || max_epochs < 0 || D < 1)
+        return fail(MLP_EINVAL, "mlp_batch_create_host: bad arguments");
+    const size_t xe = prec == MLP_BF16 ? 2 : 4;
+    size_t rows = 0, params = 0;
+    for (int t = 0; t < n_nets; ++t) {
+        if (n[t] < 0 || H[t] < 1) return fail(MLP_EINVAL, "mlp_batch_create_host: net %d has n < 0 or H < 1", t);
+        rows += (size_t)n[t];
+        params += (size_t)(D + 2) * H[t] + 1;
+    }
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    const size_t xb = rows * D * xe, yb = rows * sizeof(float), pb = params * sizeof(float);
+    const size_t lb = (size_t)n_nets * max_epochs * sizeof(double);
+    void *mem = nullptr;
+    if (cudaMalloc(&mem, al(xb) + al(yb) + al(pb) + al(lb) + 256) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(MLP_ENOMEM, "mlp_batch_create_host: cannot allocate the device copies");
+    }
+    char *xd = (char *)mem;
+    float *yd = (float *)(xd + al(xb));
+    float *pd = (float *)((char *)yd + al(yb));
+    double *ld = (double *)((char *)pd + al(pb));
+    std::vector<mlp_net_desc> descs(n_nets);
+    size_t r0 = 0, p0 = 0;
+    for (int t = 0; t < n_nets; ++t) {
+        descs[t].H = H[t];
+        descs[t].n = n[t];
+        descs[t].X = xd + r0 * D * xe;
+        descs[t].y = yd + r0;
+        descs[t].params = pd + p0;
+        descs[t].loss_hist = max_epochs > 0 ? ld + (size_t)t * max_epochs : nullptr;
+        descs[t].gnorm_hist = nullptr;
+        r0 += (size_t)n[t];
+        p0 += (size_t)(D + 2) * H[t] + 1;
+    }
+    mlp_batch_t b = nullptr;
+    mlp_status s = mlp_batch_create(prec, act, D, descs.data(), n_nets, lr, loss_mean, &b);
+    if (s) {
+        cudaFree(mem);
+        return s;
+    }
+    b->owned = mem;
+    b->xd = xd;
+    b->yd = yd;
+    b->pd = pd;
+    b->ld = ld;
+    b->x_bytes = xb;
+    b->y_bytes = yb;
+    b->p_bytes = pb;
+    b->max_epochs = max_epochs;
+    *out = b;
+    return MLP_OK;
+}
+
+mlp_status mlp_batch_run_host(mlp_batch_t b, const void *X_host, const float *y_host, const float *params_in_host,
+                              float *params_out_host, double *loss_hist_host, int32_t epochs, void *stream) {
+    if (!b) return fail(MLP_EINVAL, "mlp_batch_run_host: null plan");
+    if (!b->owned) return fail(MLP_EINVAL, "mlp_batch_run_host: the plan was not made by mlp_batch_create_host");
+    if (epochs < 0 || epochs > b->max_epochs)
+        return fail(MLP_EINVAL, "mlp_batch_run_host: epochs %d outside 0..%d", epochs, b->max_epochs);
+    if ((b->x_bytes && !X_host) || (b->y_bytes && !y_host) || (b->p_bytes && (!params_in_host || !params_out_host)))
+        return fail(MLP_EINVAL, "mlp_batch_run_host: null host buffer");
+    DeviceScope ds(b->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (b->x_bytes) CK(cudaMemcpyAsync(b->xd, X_host, b->x_bytes, cudaMemcpyHostToDevice, st), "copy X in");
+    if (b->y_bytes) CK(cudaMemcpyAsync(b->yd, y_host, b->y_bytes, cudaMemcpyHostToDevice, st), "copy y in");
+    if (b->p_bytes) CK(cudaMemcpyAsync(b->pd, params_in_host, b->p_bytes, cudaMemcpyHostToDevice, st), "copy weights in");
+    mlp_status s = mlp_batch_run(b, epochs, stream);
+    if (s) return s;
+    if (b->p_bytes)
+        CK(cudaMemcpyAsync(params_out_host, b->pd, b->p_bytes, cudaMemcpyDeviceToHost, st), "copy weights out");
+    if (loss_hist_host && epochs > 0 && b->n_nets > 0)
+        CK(cudaMemcpy2DAsync(loss_hist_host, sizeof(double) * epochs, b->ld, sizeof(double) * b->max_epochs,
+                             sizeof(double) * epochs, b->n_nets, cudaMemcpyDeviceToHost, st),
+           "copy losses out");
+    return mlp_batch_check(b, stream);
 }
 
 mlp_status mlp_batch_train(int32_t prec, int32_t act, int32_t D, const mlp_net_desc *nets, int32_t n_nets,

@@ -19,7 +19,7 @@ constexpr int BCAP = 256;        // rows staged in shared memory at a time
 template <int DP, int WU, int ACT>
 __device__ __forceinline__ void net_body(const BatchNet &nd, int D, int epochs, float lr, int loss_mean,
                                          int *status, float *Xs, float *ys, float *Wm, float *part,
-                                         float *zx, double *s_sse) {
+                                         float *zx, double *s_sse, double *s_gn) {
     // One row in flight per lane for H <= 32: at two blocks per SM the second
     // row's registers spill (measured 4.7 % slower on the 4096-net workload).
     using Eng = RowEngine<DP, WU, ACT, 1>;
@@ -58,11 +58,23 @@ __device__ __forceinline__ void net_body(const BatchNet &nd, int D, int epochs, 
         }
         eng.write_group(part, s_sse);
         __syncthreads();
+        // Update, and the FP64 squared norm of the gradient it applies: each
+        // thread's values in index order, then a fixed butterfly per warp and
+        // the warps in order.
+        // (FP64 arithmetic is slow on this part: only when asked for.)
+        double gn = 0.0;
+        const bool want_gn = nd.gnorm_hist != nullptr;
         for (int p = tid; p < P; p += BNT) {
             float g = part[p];
 #pragma unroll
             for (int q = 1; q < NG; ++q) g += part[q * P + p];
             Wm[p] -= lr * g;
+            if (want_gn) gn = fma((double)g, (double)g, gn);
+        }
+        if (want_gn) {
+            gn = warp_sum(gn);
+            if ((tid & 31) == 0) s_gn[tid >> 5] = gn;
+            __syncthreads();
         }
         if (tid == 0) {
             double t = 0.0;
@@ -70,6 +82,11 @@ __device__ __forceinline__ void net_body(const BatchNet &nd, int D, int epochs, 
             const double L = 0.5 * C * t;
             if (nd.loss_hist) nd.loss_hist[e] = L;
             if (!isfinite(L)) atomicOr(status, ST_NONFINITE);
+            if (nd.gnorm_hist) {
+                double u = 0.0;
+                for (int q = 0; q < RE_NW; ++q) u += s_gn[q];
+                nd.gnorm_hist[e] = sqrt(u);
+            }
         }
         __syncthreads();
     }
@@ -84,6 +101,7 @@ __global__ void __launch_bounds__(BNT, (DP <= 36 ? 2 : 1)) k_batched_train(const
                                                          int part_floats, int wm_floats) {
     extern __shared__ __align__(16) float smem[];
     __shared__ double s_sse[RE_NW];
+    __shared__ double s_gn[RE_NW];
     float *Xs = smem;                      // BCAP x DP
     float *ys = Xs + BCAP * DP;            // BCAP
     float *Wm = ys + BCAP;                 // wm_floats
@@ -94,16 +112,19 @@ __global__ void __launch_bounds__(BNT, (DP <= 36 ? 2 : 1)) k_batched_train(const
     for (int idx = blockIdx.x; idx < n_nets; idx += gridDim.x) {
         const BatchNet nd = nets[order ? order[idx] : idx];
         if (nd.n <= 0 || nd.H <= 0) {
-            if (nd.loss_hist && threadIdx.x == 0)
-                for (int e = 0; e < epochs; ++e) nd.loss_hist[e] = 0.0;
+            if (threadIdx.x == 0)
+                for (int e = 0; e < epochs; ++e) {
+                    if (nd.loss_hist) nd.loss_hist[e] = 0.0;
+                    if (nd.gnorm_hist) nd.gnorm_hist[e] = 0.0;
+                }
             continue;
         }
         if (nd.H <= 32)
-            net_body<DP, 1, ACT>(nd, D, epochs, lr, loss_mean, status, Xs, ys, Wm, part, zx, s_sse);
+            net_body<DP, 1, ACT>(nd, D, epochs, lr, loss_mean, status, Xs, ys, Wm, part, zx, s_sse, s_gn);
         else if (nd.H <= 64)
-            net_body<DP, 2, ACT>(nd, D, epochs, lr, loss_mean, status, Xs, ys, Wm, part, zx, s_sse);
+            net_body<DP, 2, ACT>(nd, D, epochs, lr, loss_mean, status, Xs, ys, Wm, part, zx, s_sse, s_gn);
         else
-            net_body<DP, 4, ACT>(nd, D, epochs, lr, loss_mean, status, Xs, ys, Wm, part, zx, s_sse);
+            net_body<DP, 4, ACT>(nd, D, epochs, lr, loss_mean, status, Xs, ys, Wm, part, zx, s_sse, s_gn);
     }
 }
 
@@ -124,6 +145,13 @@ int dp_for(int D) {
 
 }  // namespace
 
+bool batched_shape_supported(int D, int shape) {
+    if (shape == BATCH_SHAPE_U1) return dp_for(D) != 0;
+    if (shape == BATCH_SHAPE_U2_RB1) return batched_u2_supported(D, 1);
+    if (shape == BATCH_SHAPE_U2_RB2) return batched_u2_supported(D, 2);
+    return false;
+}
+
 int batched_max_H() { return 128; }
 int batched_max_D() { return 64; }
 
@@ -137,7 +165,10 @@ void batched_smem_layout(int D, int Hmax, int *part_floats, int *wm_floats, size
 }
 
 cudaError_t batched_train(int act, int D, int Hmax, const BatchNet *nets_dev, const int *order_dev, int n_nets,
-                          int epochs, float lr, int loss_mean, int *status, cudaStream_t st) {
+                          int epochs, float lr, int loss_mean, int *status, int shape, cudaStream_t st) {
+    if (shape != BATCH_SHAPE_U1)
+        return batched_train_u2(act, D, Hmax, nets_dev, order_dev, n_nets, epochs, lr, loss_mean, status,
+                                shape == BATCH_SHAPE_U2_RB2 ? 2 : 1, st);
     const int DP = dp_for(D);
     if (DP == 0 || Hmax > 128) return cudaErrorInvalidValue;
     if (n_nets == 0 || epochs == 0) return cudaSuccess;

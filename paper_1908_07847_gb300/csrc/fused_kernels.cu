@@ -216,20 +216,24 @@ __global__ void __launch_bounds__(FNT, 1) k_fused_train(FArgs a) {
                 __syncthreads();
                 continue;
             }
+            // Each of the G block partials stays below 2^63 / G in magnitude, so
+            // their integer sum cannot wrap; a partial beyond that (or NaN) is
+            // flagged as non-finite instead of silently corrupting the update.
+            const float lim = 9.2e18f / (float)G;
             int bad = 0;
             for (int p = tid; p < P; p += FNT) {
                 float s = gpart[p];
 #pragma unroll
                 for (int q = 1; q < NG; ++q) s += gpart[q * P + p];
                 const float v = s * gup;
-                if (!(fabsf(v) < 4.0e18f)) bad = 1;   // out of range or NaN
+                if (!(fabsf(v) < lim)) bad = 1;   // out of range or NaN
                 red_add(acc + p, __float2ll_rn(v));
             }
             if (tid == 0) {
                 double t = 0.0;
                 for (int q = 0; q < NG; ++q) t += s_red[q];
                 const double v = t * 4294967296.0;
-                if (!(v < 4.0e18)) bad = 1;
+                if (!(v < (double)lim)) bad = 1;
                 red_add(acc + P, __double2ll_rn(v));
             }
             if (bad) atomicOr(a.status, ST_NONFINITE);

@@ -238,6 +238,7 @@ struct BatchNet {
     const float *y;      // n labels
     float *params;       // packed [W1, b1, w2, b2], trained in place
     double *loss_hist;   // [epochs] or NULL
+    double *gnorm_hist;  // [epochs] or NULL
     int64_t n;
     int32_t H;
     int32_t pad;
@@ -246,8 +247,17 @@ struct BatchNet {
 int batched_max_H();
 int batched_max_D();
 void batched_smem_layout(int D, int Hmax, int *part_floats, int *wm_floats, size_t *bytes);
+
+// Kernel shapes of the FP32 many-nets launch (the tuning knob of a plan).
+constexpr int BATCH_SHAPE_U1 = 0;      // one hidden unit a lane, blocks of 8 warps, two per SM
+constexpr int BATCH_SHAPE_U2_RB1 = 1;  // two units a lane, blocks of 4 warps, two per SM, one row in flight
+constexpr int BATCH_SHAPE_U2_RB2 = 2;  // the same with two rows in flight (D = 33 only)
+bool batched_shape_supported(int D, int shape);
 cudaError_t batched_train(int act, int D, int Hmax, const BatchNet *nets_dev, const int *order_dev, int n_nets,
-                          int epochs, float lr, int loss_mean, int *status, cudaStream_t st);
+                          int epochs, float lr, int loss_mean, int *status, int shape, cudaStream_t st);
+cudaError_t batched_train_u2(int act, int D, int Hmax, const BatchNet *nets_dev, const int *order_dev, int n_nets,
+                             int epochs, float lr, int loss_mean, int *status, int rb, cudaStream_t st);
+bool batched_u2_supported(int D, int rb);
 
 // ------------------------------------------- bf16 tensor-core (tcgen05) path
 
@@ -255,10 +265,10 @@ bool tc_supported(int D, int H);
 size_t tc_desc_bytes();
 size_t tc_tmap_bytes();
 cudaError_t tc_encode_map(void *map, const void *X, int D, int64_t n);
-void tc_fill_desc(void *desc, const void *tmap_dev, const float *y, float *params, double *loss_hist, int64_t n,
-                  int H);
+void tc_fill_desc(void *desc, const void *tmap_dev, const float *y, float *params, double *loss_hist,
+                  double *gnorm_hist, int64_t n, int H);
 cudaError_t tc_batched_train(const void *descs_dev, const int *order_dev, int n_nets, int D, int epochs, float lr,
-                             int loss_mean, int *status, cudaStream_t st);
+                             int loss_mean, int act, int *status, cudaStream_t st);
 
 // One wide network (H = 256..2048, a multiple of 256) trained by clusters of
 // H/256 blocks; scratch of tc_cluster_scratch_bytes(), all zero before the first
@@ -266,9 +276,13 @@ cudaError_t tc_batched_train(const void *descs_dev, const int *order_dev, int n_
 bool tc_cluster_supported(int D, int H);
 size_t tc_cluster_scratch_bytes(int D, int H);
 int tc_cluster_max_clusters(int H);
+// gnorm_hist (may be NULL) needs gn_part, (H/256 + 1) x epochs doubles of
+// device scratch.  A device that refuses the cooperative cluster launch makes
+// the call fail with that launch's error.
 cudaError_t tc_cluster_train(const void *X, const float *y, float *params, int D, int H, int64_t n, int epochs,
-                             int64_t mb, float lr, int loss_mean, double *loss_hist, int *status, void *scratch,
-                             int max_clusters, FusedCounters *ctr, cudaStream_t st);
+                             int64_t mb, float lr, int loss_mean, int act, double *loss_hist, double *gnorm_hist,
+                             double *gn_part, int *status, void *scratch, int max_clusters, FusedCounters *ctr,
+                             cudaStream_t st);
 
 int device_sm_count();
 

@@ -1,11 +1,9 @@
 // mlp_train_fused_noalloc: the fused training kernel run on caller-owned
 // weights with its scratch in a fixed device array, so that the call allocates
-// no device memory.  For callers that cannot allocate: code that runs while a
-// stream is being captured into a CUDA graph, or inside a framework that owns
-// every byte of device memory through its own pool, or a real-time loop that
-// must not block on the allocator.
-#include <mutex>
-
+// no device memory.  For callers that cannot allocate: code inside a framework
+// that hands out every byte of device memory from its own pool (a cudaMalloc
+// beside the pool would fail or fragment it), or a real-time loop that must not
+// block on the allocator's device-wide synchronisation.
 #include "mlp_internal.cuh"
 
 namespace {
@@ -25,21 +23,17 @@ constexpr size_t NA_BYTES = NA_SCRATCH + 256;
 // (any two streams, any two threads) race and must not be issued that way.
 __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
 
-// The array's device address, looked up once per device with that device
-// current.  In host code the name g_noalloc_scratch is only a host-side
-// stand-in for the symbol; kernels must be given this address instead.
-cudaError_t scratch_address(int dev, unsigned char **out) {
-    static std::mutex mu;
-    static unsigned char *addr[256] = {};
-    if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lk(mu);
-    if (!addr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        addr[dev] = (unsigned char *)p;
-    }
-    *out = addr[dev];
+// The array's device address on the current device.  In host code the name
+// g_noalloc_scratch is only a host-side stand-in for the symbol; kernels must
+// be given this address instead.  It is looked up on every call (the lookup
+// allocates nothing): after cudaDeviceReset, or any other teardown of the
+// device's primary context, the module is loaded again and the array may sit
+// at a new address, so a cached one could be stale.
+cudaError_t scratch_address(unsigned char **out) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    *out = (unsigned char *)p;
     return cudaSuccess;
 }
 
@@ -62,10 +56,8 @@ extern "C" mlp_status mlp_train_fused_noalloc(int32_t act, int32_t D, int32_t H,
     if (((uintptr_t)params & 15) != 0)
         return noalloc_fail(MLP_EINVAL, "mlp_train_fused_noalloc: params must be 16-byte aligned");
     cudaStream_t st = (cudaStream_t)stream;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return noalloc_fail(MLP_ECUDA, "mlp_train_fused_noalloc: no device");
     unsigned char *base = nullptr;
-    if (scratch_address(dev, &base) != cudaSuccess)
+    if (scratch_address(&base) != cudaSuccess)
         return noalloc_fail(MLP_ECUDA, "mlp_train_fused_noalloc: cannot resolve the scratch array");
     int *status = (int *)(base + NA_SCRATCH);
     const size_t need = mlp::fused_scratch_bytes(D, H, 0);

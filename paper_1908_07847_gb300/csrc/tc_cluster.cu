@@ -1,6 +1,7 @@
 // BF16 tensor-core (tcgen05) training of one wide network (H = 256 x S hidden
 // units, S <= 8) by mini-batch gradient descent (Sec. 2.2 of arXiv 1908.07847:
-// feed-forward, output error, backpropagation, w <- w - lr g, no momentum).
+// feed-forward, output error, backpropagation, w <- w - lr g, no momentum),
+// with sigmoid (Eq. 1) or tanh hidden units.
 //
 // The grid is made of clusters of S blocks; block c of a cluster owns hidden
 // units [256 c, 256 c + 256).  Per step (one mini-batch of m rows), cluster k
@@ -68,11 +69,13 @@ struct ClArgs {
     unsigned long long *bar;      // per-slice barrier arrivals, 16 apart
     unsigned long long bar_base;  // value at launch
     double *loss_hist;
+    double *gn_part;              // [epochs][S + 1] or NULL: slice squared norms, then gb2
     int *status;
     int64_t n, mb;
     int D, H, epochs;
     float lr;
     int loss_mean;
+    int act;                      // hidden activation (mlp_activation)
 };
 
 __device__ __forceinline__ uint32_t cluster_rank() {
@@ -97,6 +100,7 @@ __device__ __forceinline__ void cluster_sync_all() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
+template <int ACT>
 __global__ void __launch_bounds__(NT, 1) k_tc_cluster(const __grid_constant__ CUtensorMap tmap, ClArgs a) {
     // Launch-shape check before any tensor-memory, cluster or peer access: the
     // kernel needs clusters of exactly H/256 blocks of NT threads.
@@ -126,10 +130,19 @@ __global__ void __launch_bounds__(NT, 1) k_tc_cluster(const __grid_constant__ CU
     uint32_t *tmem_slot = (uint32_t *)(sm + SM_MISC);
     volatile int *abort = (volatile int *)(sm + SM_MISC + 16);
     float *red = (float *)(sm + SM_MISC + 64);
+    double *gnw = (double *)(sm + SM_MISC + 128);   // 8 epilogue warps' squared gradient norms
     float *zx = (float *)(sm + SM_ZX);
     const float *zrb = (const float *)(sm + SM_ZR);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int D = a.D, H = a.H;
+    // Hidden activation from the forward accumulator: the sigmoid as
+    // 1/2 + tanh(z/2)/2 (the operands hold W1/2 and b1/2, so the accumulator
+    // is z/2), tanh (Sec. 2.2's other activation) directly from z.
+    constexpr bool tanh_act = ACT == MLP_ACT_TANH;
+    constexpr float wscale = tanh_act ? 1.0f : 0.5f;
+    // h = act_a tanh(acc) + act_b; the tanh form keeps the sigmoid's instruction
+    // pattern (one packed fma after the tanh)
+    constexpr uint32_t act_a = tanh_act ? BF2_ONE : BF2_HALF, act_b = tanh_act ? 0u : BF2_HALF;
     const int S = H / HS;                            // blocks per cluster
     const int crank = (int)cluster_rank();
     const int k = blockIdx.x / S, K = gridDim.x / S;
@@ -187,14 +200,14 @@ __global__ void __launch_bounds__(NT, 1) k_tc_cluster(const __grid_constant__ CU
             tmem_st16(lane_base + TM_WM + DMAX * half + c16, w);
 #pragma unroll
             for (int u = 0; u < 16; ++u)
-                *(__nv_bfloat16 *)(sm + SM_W1 + kmajor_off(jl, c16 + u)) = __float2bfloat16_rn(0.5f * w[u]);
+                *(__nv_bfloat16 *)(sm + SM_W1 + kmajor_off(jl, c16 + u)) = __float2bfloat16_rn(wscale * w[u]);
         }
 #pragma unroll
         for (int kk = DMAX; kk < 64; ++kk) *(__nv_bfloat16 *)(sm + SM_W1 + kmajor_off(jl, kk)) = __float2bfloat16_rn(0.f);
         b1s[jl] = a.params[HD + j];
         w2s[jl] = a.params[HD + H + j];
         w2b[jl] = __float2bfloat16_rn(w2s[jl]);
-        *(__nv_bfloat16 *)(sm + SM_B1T + k16_off(jl, 0)) = __float2bfloat16_rn(0.5f * b1s[jl]);
+        *(__nv_bfloat16 *)(sm + SM_B1T + k16_off(jl, 0)) = __float2bfloat16_rn(wscale * b1s[jl]);
     }
     proxy_fence();
     tc_fence_before();
@@ -215,6 +228,10 @@ __global__ void __launch_bounds__(NT, 1) k_tc_cluster(const __grid_constant__ CU
     int z1f_use = 0, he_use = 0, de_use = 0, epi_use = 0, tcount = 0;
     double sse_epoch = 0.0;
     bool ok = !*abort;
+    // A launch that starts after an unread timeout does nothing, and no block
+    // of its cluster sends it anything (all of them read the same status as
+    // they start together).
+    const bool skipped = !ok;
     int64_t step = 0;
     auto epi_sync = [&]() -> bool {
         mbar_arrive(BAR_EPI);
@@ -309,7 +326,7 @@ __global__ void __launch_bounds__(NT, 1) k_tc_cluster(const __grid_constant__ CU
                         float z[32];
                         tmem_ld32(lane_base + TM_Z1 + c0, z);
 #pragma unroll
-                        for (int u = 0; u < 16; ++u) hp[16 * ch + u] = sigmoid_half_bf2(pack_bf16(z[2 * u], z[2 * u + 1]));
+                        for (int u = 0; u < 16; ++u) hp[16 * ch + u] = hfma2(tanh_bf2(pack_bf16(z[2 * u], z[2 * u + 1])), act_a, act_b);
 #pragma unroll
                         for (int u = 0; u < 16; u += 4) {
                             const uint4 w = *(const uint4 *)(w2b + c0 + 2 * u);
@@ -355,7 +372,7 @@ __global__ void __launch_bounds__(NT, 1) k_tc_cluster(const __grid_constant__ CU
                                 st_async_v4(remote_addr(src, (uint32_t)cr), v, remote_addr(zbar, (uint32_t)cr));
                         }
                     }
-                    // while the shares travel: u = w2 h (1 - h) in bf16 pairs, in place
+                    // while the shares travel: u = w2 f'(h) in bf16 pairs, in place
 #pragma unroll
                     for (int ch = 0; ch < 16; ++ch) {
                         const uint4 wv = *(const uint4 *)(w2b + cb + 8 * ch);
@@ -363,7 +380,9 @@ __global__ void __launch_bounds__(NT, 1) k_tc_cluster(const __grid_constant__ CU
 #pragma unroll
                         for (int v = 0; v < 4; ++v) {
                             const uint32_t h = hp[4 * ch + v];
-                            hp[4 * ch + v] = hmul2(wp[v], hmul2(h, hfma2(h, BF2_NEG1, BF2_ONE)));
+                            // f'(h): h (1 - h) for the sigmoid, 1 - h^2 for tanh
+                            hp[4 * ch + v] = tanh_act ? hmul2(wp[v], hfma2(h ^ 0x80008000u, h, BF2_ONE))
+                                                      : hmul2(wp[v], hmul2(h, hfma2(h, BF2_NEG1, BF2_ONE)));
                         }
                     }
                     if (!mbar_wait(zbar, (tcount >> 1) & 1, abort)) { eok = false; break; }
@@ -495,6 +514,9 @@ __global__ void __launch_bounds__(NT, 1) k_tc_cluster(const __grid_constant__ CU
                 ok = false;
                 break;
             }
+            // the epoch's last update: cluster 0's blocks record the squared
+            // norm of their slice of the gradient (FP64, fixed order)
+            const bool want_gn = a.gn_part && k == 0 && b0 + mbs >= a.n;
             if (warp >= 2) {
                 const int jl = half * 128 + r;
                 const float *gs = a.sum + (size_t)crank * E + jl;
@@ -511,14 +533,21 @@ __global__ void __launch_bounds__(NT, 1) k_tc_cluster(const __grid_constant__ CU
 #pragma unroll
                     for (int u = 0; u < 16; ++u) {
                         w[u] -= a.lr * g[c16 + u];   // columns >= D stay 0
-                        *(__nv_bfloat16 *)(sm + SM_W1 + kmajor_off(jl, c16 + u)) = __float2bfloat16_rn(0.5f * w[u]);
+                        *(__nv_bfloat16 *)(sm + SM_W1 + kmajor_off(jl, c16 + u)) = __float2bfloat16_rn(wscale * w[u]);
                     }
                     tmem_st16(lane_base + TM_WM + DMAX * half + c16, w);
+                }
+                if (want_gn) {
+                    double gn = 0.0;
+#pragma unroll
+                    for (int kk = 0; kk < DMAX + 2; ++kk) gn = fma((double)g[kk], (double)g[kk], gn);
+                    gn = warp_sum(gn);
+                    if (lane == 0) gnw[warp - 2] = gn;
                 }
                 b1s[jl] -= a.lr * g[DMAX];
                 w2s[jl] -= a.lr * g[DMAX + 1];
                 w2b[jl] = __float2bfloat16_rn(w2s[jl]);
-                *(__nv_bfloat16 *)(sm + SM_B1T + k16_off(jl, 0)) = __float2bfloat16_rn(0.5f * b1s[jl]);
+                *(__nv_bfloat16 *)(sm + SM_B1T + k16_off(jl, 0)) = __float2bfloat16_rn(wscale * b1s[jl]);
             }
             b2 -= a.lr * red[8];
             if (k == 0 && crank == 0 && tid == 64) {
@@ -532,9 +561,16 @@ __global__ void __launch_bounds__(NT, 1) k_tc_cluster(const __grid_constant__ CU
             tc_fence_before();
             __syncthreads();
             tc_fence_after();
+            if (want_gn && tid == 64) {
+                double u = 0.0;
+                for (int w = 0; w < NEPI; ++w) u += gnw[w];
+                a.gn_part[(size_t)e * (S + 1) + crank] = u;
+                if (crank == 0) a.gn_part[(size_t)e * (S + 1) + S] = (double)red[8];
+            }
         }
     }
-    const bool aborted = *abort;
+    // a failed step-end barrier stops the block without raising its flag
+    const bool aborted = *abort || (!ok && !skipped);
     if (aborted && tid == 0) atomicOr(a.status, ST_TIMEOUT);
     if (k == 0 && !aborted) {
         if (warp >= 2) {
@@ -562,9 +598,36 @@ __global__ void __launch_bounds__(NT, 1) k_tc_cluster(const __grid_constant__ CU
             mbar_wait(BAR_FULL + 8 * (qd % NSTAGE), (qd / NSTAGE) & 1, abort, true);
     tc_fence_before();
     __syncthreads();
+    // Every block of the cluster stops here, so after this barrier no peer
+    // issues another z2 share.  Every wait on the way is bounded, so every
+    // block gets here.
     cluster_sync_all();
+    if (aborted && !skipped && tid == 64) {
+        // Shares a peer issued before stopping may still be landing in this
+        // block's receive buffers (the st.async stores are tracked only by the
+        // receive barriers).  Only the tiles tcount and tcount + 1 can have
+        // any: a peer sends tile t + 1's share only after it has received
+        // every share of tile t, this block's included.  Wait (bounded) for
+        // both phases, so that nothing targets this block's shared memory
+        // once it has left; a phase whose sender stopped first never
+        // completes and the wait gives up after the time limit.
+        for (int t = tcount; t < tcount + 2; ++t)
+            mbar_wait((t & 1) ? BAR_ZR1 : BAR_ZR0, (t >> 1) & 1, abort, true);
+    }
+    __syncthreads();
     tc_fence_after();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
+}
+
+// gnorm[e] = sqrt(sum over slices of their squared norms + gb2^2), in slice
+// order (the slices' values come from cluster 0's blocks).
+__global__ void k_cluster_gnorm(const double *part, int S, int epochs, double *gnorm) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < epochs; e += gridDim.x * blockDim.x) {
+        const double *p = part + (size_t)e * (S + 1);
+        double u = 0.0;
+        for (int c = 0; c < S; ++c) u += p[c];
+        gnorm[e] = sqrt(fma(p[S], p[S], u));
+    }
 }
 
 }  // namespace
@@ -587,7 +650,7 @@ int tc_cluster_max_clusters(int H) {
     const int S = H / HS;
     std::lock_guard<std::mutex> lk(mu);
     if (cache[S] == 0) {
-        cudaFuncSetAttribute(k_tc_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM_ALLOC);
+        cudaFuncSetAttribute(k_tc_cluster<MLP_ACT_SIGMOID>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM_ALLOC);
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)S);
         cfg.blockDim = dim3(NT);
@@ -600,7 +663,8 @@ int tc_cluster_max_clusters(int H) {
         cfg.attrs = at;
         cfg.numAttrs = 1;
         int n = 0;
-        if (cudaOccupancyMaxActiveClusters(&n, (void *)k_tc_cluster, &cfg) != cudaSuccess || n < 1) {
+        // (both activations' instantiations use the same resources)
+        if (cudaOccupancyMaxActiveClusters(&n, (void *)k_tc_cluster<MLP_ACT_SIGMOID>, &cfg) != cudaSuccess || n < 1) {
             cudaGetLastError();
             n = 1;
         }
@@ -610,8 +674,9 @@ int tc_cluster_max_clusters(int H) {
 }
 
 cudaError_t tc_cluster_train(const void *X, const float *y, float *params, int D, int H, int64_t n, int epochs,
-                             int64_t mb, float lr, int loss_mean, double *loss_hist, int *status, void *scratch,
-                             int max_clusters, FusedCounters *ctr, cudaStream_t st) {
+                             int64_t mb, float lr, int loss_mean, int act, double *loss_hist, double *gnorm_hist,
+                             double *gn_part, int *status, void *scratch, int max_clusters, FusedCounters *ctr,
+                             cudaStream_t st) {
     if (!tc_cluster_supported(D, H)) return cudaErrorInvalidValue;
     if (n <= 0 || epochs <= 0) return cudaSuccess;
     const int S = H / HS;
@@ -624,7 +689,8 @@ cudaError_t tc_cluster_train(const void *X, const float *y, float *params, int D
     CUtensorMap tmap;
     cudaError_t e = tc_encode_map(&tmap, X, D, n);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_tc_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM_ALLOC);
+    auto kern = act == MLP_ACT_TANH ? k_tc_cluster<MLP_ACT_TANH> : k_tc_cluster<MLP_ACT_SIGMOID>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM_ALLOC);
     if (e != cudaSuccess) return e;
     const size_t E = (size_t)(D + 2) * HS, Kmax = (size_t)tc_cluster_max_clusters(H);
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
@@ -641,6 +707,7 @@ cudaError_t tc_cluster_train(const void *X, const float *y, float *params, int D
     a.bar = (unsigned long long *)b;
     a.bar_base = ctr->bar;
     a.loss_hist = loss_hist;
+    a.gn_part = gnorm_hist ? gn_part : nullptr;
     a.status = status;
     a.n = n;
     a.mb = mb;
@@ -649,6 +716,7 @@ cudaError_t tc_cluster_train(const void *X, const float *y, float *params, int D
     a.epochs = epochs;
     a.lr = lr;
     a.loss_mean = loss_mean;
+    a.act = act;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(K * S));
     cfg.blockDim = dim3(NT);
@@ -663,18 +731,18 @@ cudaError_t tc_cluster_train(const void *X, const float *y, float *params, int D
     at[1].val.cooperative = 1;
     cfg.attrs = at;
     cfg.numAttrs = 2;
-    e = cudaLaunchKernelEx(&cfg, k_tc_cluster, tmap, a);
-    if (e != cudaSuccess) {
-        // Without cooperative cluster launches the grid still fits the device
-        // at once (K is the occupancy limit); the grid barrier's waits are
-        // bounded either way.
-        cudaGetLastError();
-        cfg.numAttrs = 1;
-        e = cudaLaunchKernelEx(&cfg, k_tc_cluster, tmap, a);
-        if (e != cudaSuccess) return e;
-    }
+    // Only a cooperative launch guarantees that every cluster is resident at
+    // once, which the step-end barriers between clusters need; if the device
+    // refuses it, the call fails (there is no launch without that guarantee).
+    e = cudaLaunchKernelEx(&cfg, kern, tmap, a);
+    if (e != cudaSuccess) return e;
     const int64_t steps = ((n + mbs - 1) / mbs) * (int64_t)epochs;
     ctr->bar += 2ull * (unsigned long long)K * (unsigned long long)steps;   // every slice's counter
+    if (gnorm_hist) {
+        k_cluster_gnorm<<<(epochs + 127) / 128, 128, 0, st>>>(gn_part, S, epochs, gnorm_hist);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     return cudaSuccess;
 }
 

@@ -9,9 +9,10 @@
 //                                    ones column against b1/2; FP32 accumulator
 //                                    in tensor memory holds z1/2;
 //   epilogue   thread r of 4 warps owns row r (= tensor-memory lane r):
-//              h = sigmoid(z1) = 1/2 + tanh(z1/2)/2 in bf16 pairs, z2 = h w2 + b2
+//              h = sigmoid(z1) = 1/2 + tanh(z1/2)/2 in bf16 pairs (or, for tanh
+//              hidden units, h = tanh(z1) with W1 and b1 unscaled), z2 = h w2 + b2
 //              (FP32), o = sigmoid(z2), d2 = c (o - y) o (1 - o),
-//              u = w2 h (1 - h) and d1 = d2 u in bf16 pairs;
+//              u = w2 f'(h) and d1 = d2 u in bf16 pairs;
 //              h and d1 go to shared memory as bf16, transposed on the fly
 //              (MN-major operand tiles), d2 to a small K-major operand;
 //   gradient   gW1 += d1^T X         M = 128 hidden units, N = 64, K = 128 rows,
@@ -67,11 +68,13 @@ constexpr uint32_t SM_TOTAL = SM_ZX + 2 * 2 * 128 * 4;
 constexpr uint32_t SM_ALLOC = SM_TOTAL + 1024;             // + alignment slack
 static_assert(SM_ALLOC <= 227 * 1024, "shared memory");
 
-struct TcNet {
+// 16-byte aligned: the host packs the descriptors sizeof(TcNet) apart.
+struct __align__(16) TcNet {
     const CUtensorMap *tmap;  // X: bf16 [n x D], box 64 x 128, 128-byte swizzle
     const float *y;           // n labels
     float *params;            // packed FP32 [W1 (H x D), b1, w2, b2]
     double *loss_hist;        // [epochs] or NULL
+    double *gnorm_hist;       // [epochs] or NULL
     int64_t n;
     int32_t H;
     int32_t pad;
@@ -85,11 +88,13 @@ struct TcArgs {
     int epochs;
     float lr;
     int loss_mean;
+    int act;                  // hidden activation (mlp_activation)
     int *status;
 };
 
 using namespace tcd;
 
+template <int ACT>
 __global__ void __launch_bounds__(NT, 1) k_tc_batched(TcArgs a) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *sm = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -107,8 +112,17 @@ __global__ void __launch_bounds__(NT, 1) k_tc_batched(TcArgs a) {
     uint32_t *tmem_slot = (uint32_t *)(sm + SM_MISC);
     volatile int *abort = (volatile int *)(sm + SM_MISC + 16);
     float *red = (float *)(sm + SM_MISC + 64);     // 4 warps x (sse, gb2)
+    double *gnr = (double *)(sm + SM_MISC + 128);  // 8 epilogue warps' squared gradient norms
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int D = a.D;
+    // Hidden activation from the forward accumulator: the sigmoid as
+    // 1/2 + tanh(z/2)/2 (the operands hold W1/2 and b1/2, so the accumulator
+    // is z/2), tanh (Sec. 2.2's other activation) directly from z.
+    constexpr bool tanh_act = ACT == MLP_ACT_TANH;
+    constexpr float wscale = tanh_act ? 1.0f : 0.5f;
+    // h = act_a tanh(acc) + act_b; the tanh form keeps the sigmoid's instruction
+    // pattern (one packed fma after the tanh)
+    constexpr uint32_t act_a = tanh_act ? BF2_ONE : BF2_HALF, act_b = tanh_act ? 0u : BF2_HALF;
     const uint32_t bars[12] = {BAR_FULL, BAR_FULL + 8, BAR_EMPTY, BAR_EMPTY + 8, BAR_Z1F, BAR_Z1E,
                                BAR_HF,   BAR_HE,       BAR_DF,    BAR_DE,        BAR_EPOCH, BAR_W};
     const uint32_t counts[12] = {1, 1, 1, 1, 1, NEPI_T, NEPI_T, 1, NEPI_T, 1, 1, NEPI_T};
@@ -151,13 +165,13 @@ __global__ void __launch_bounds__(NT, 1) k_tc_batched(TcArgs a) {
         for (int i = tid; i < H * 64; i += NT) {
             const int j = i >> 6, k = i & 63;
             const float v = (k < D) ? P[j * D + k] : 0.f;
-            *(__nv_bfloat16 *)(sm + SM_W1 + kmajor_off(j, k)) = __float2bfloat16_rn(0.5f * v);
+            *(__nv_bfloat16 *)(sm + SM_W1 + kmajor_off(j, k)) = __float2bfloat16_rn(wscale * v);
         }
         for (int j = tid; j < H; j += NT) {
             b1s[j] = P[HD + j];
             w2s[j] = P[HD + H + j];
             w2b[j] = __float2bfloat16_rn(w2s[j]);
-            *(__nv_bfloat16 *)(sm + SM_B1T + k16_off(j, 0)) = __float2bfloat16_rn(0.5f * b1s[j]);
+            *(__nv_bfloat16 *)(sm + SM_B1T + k16_off(j, 0)) = __float2bfloat16_rn(wscale * b1s[j]);
         }
         proxy_fence();
         tc_fence_before();
@@ -166,8 +180,11 @@ __global__ void __launch_bounds__(NT, 1) k_tc_batched(TcArgs a) {
         float b2 = P[HD + 2 * H];
 
         if (T == 0 || a.epochs == 0) {
-            if (nd.loss_hist && tid == 0)
-                for (int e = 0; e < a.epochs; ++e) nd.loss_hist[e] = 0.0;
+            if (tid == 0)
+                for (int e = 0; e < a.epochs; ++e) {
+                    if (nd.loss_hist) nd.loss_hist[e] = 0.0;
+                    if (nd.gnorm_hist) nd.gnorm_hist[e] = 0.0;
+                }
             continue;
         }
 
@@ -299,7 +316,7 @@ __global__ void __launch_bounds__(NT, 1) k_tc_batched(TcArgs a) {
                         float z[32];
                         tmem_ld32(lane_base + TM_Z1 + c0, z);
 #pragma unroll
-                        for (int u = 0; u < 16; ++u) hp[16 * ch + u] = sigmoid_half_bf2(pack_bf16(z[2 * u], z[2 * u + 1]));
+                        for (int u = 0; u < 16; ++u) hp[16 * ch + u] = hfma2(tanh_bf2(pack_bf16(z[2 * u], z[2 * u + 1])), act_a, act_b);
 #pragma unroll
                         for (int u = 0; u < 16; u += 4) {
                             const uint4 w = *(const uint4 *)(w2b + c0 + 2 * u);
@@ -329,7 +346,7 @@ __global__ void __launch_bounds__(NT, 1) k_tc_batched(TcArgs a) {
                     tc_fence_before();
                     mbar_arrive(BAR_Z1E);  // Z1 in tensor memory may be overwritten
                     // the two halves' shares of z2 meet in shared memory; while the
-                    // other half arrives: u = w2 h (1 - h) in bf16 pairs, in place
+                    // other half arrives: u = w2 f'(h) in bf16 pairs, in place
                     float *zxp = zx + (tcount & 1) * 256;
                     zxp[half * 128 + r] = (zp[0] + zp[1]) + (zp[2] + zp[3]);
                     mbar_arrive(BAR_EPI);
@@ -341,7 +358,9 @@ __global__ void __launch_bounds__(NT, 1) k_tc_batched(TcArgs a) {
 #pragma unroll
                         for (int v = 0; v < 4; ++v) {
                             const uint32_t h = hp[4 * ch + v];
-                            hp[4 * ch + v] = hmul2(wp[v], hmul2(h, hfma2(h, BF2_NEG1, BF2_ONE)));
+                            // f'(h): h (1 - h) for the sigmoid, 1 - h^2 for tanh
+                            hp[4 * ch + v] = tanh_act ? hmul2(wp[v], hfma2(h ^ 0x80008000u, h, BF2_ONE))
+                                                      : hmul2(wp[v], hmul2(h, hfma2(h, BF2_NEG1, BF2_ONE)));
                         }
                     }
                     if (!mbar_wait(BAR_EPI, epi_use++ & 1, abort)) { ok = false; break; }
@@ -411,6 +430,8 @@ __global__ void __launch_bounds__(NT, 1) k_tc_batched(TcArgs a) {
                         for (int u = 0; u < 16; ++u)
                             if (c16 + u < D) gs[j * D + c16 + u] = g[u];
                     }
+                    gs[HD + j] = gb1;       // kept for the gradient norm
+                    gs[HD + H + j] = gw2;
                     const float nb1 = b1s[j] - a.lr * gb1;
                     const float nw2 = w2s[j] - a.lr * gw2;
                     P[HD + j] = nb1;
@@ -418,9 +439,23 @@ __global__ void __launch_bounds__(NT, 1) k_tc_batched(TcArgs a) {
                     b1s[j] = nb1;
                     w2s[j] = nw2;
                     w2b[j] = __float2bfloat16_rn(nw2);
-                    *(__nv_bfloat16 *)(sm + SM_B1T + k16_off(j, 0)) = __float2bfloat16_rn(0.5f * nb1);
+                    *(__nv_bfloat16 *)(sm + SM_B1T + k16_off(j, 0)) = __float2bfloat16_rn(wscale * nb1);
                 }
                 if (!epi_sync()) { ok = false; break; }
+                // FP64 squared norm of the gradient this update applies (only
+                // when asked for): each thread's elements of [gW1, gb1, gw2] in
+                // index order, a fixed butterfly per warp, the warps in order,
+                // then gb2
+                // (the pointer is read here, not kept in registers for the epoch)
+                double *const gnorm_hist = a.nets[a.order ? a.order[idx] : idx].gnorm_hist;
+                const bool want_gn = gnorm_hist != nullptr;
+                if (want_gn) {
+                    double gn = 0.0;
+                    for (int i = (warp - 2) * 32 + lane; i < HD + 2 * H; i += (int)NEPI_T)
+                        gn = fma((double)gs[i], (double)gs[i], gn);
+                    gn = warp_sum(gn);
+                    if (lane == 0) gnr[warp - 2] = gn;
+                }
                 {
                     // w -= lr g over the flat H x D array, 16 loads in flight per thread
                     const int et = (warp - 2) * 32 + lane;   // epilogue thread 0..255
@@ -438,7 +473,7 @@ __global__ void __launch_bounds__(NT, 1) k_tc_batched(TcArgs a) {
                                 const int j = i / D, k = i - j * D;
                                 w[v] -= a.lr * gs[i];
                                 P[i] = w[v];
-                                *(__nv_bfloat16 *)(sm + SM_W1 + kmajor_off(j, k)) = __float2bfloat16_rn(0.5f * w[v]);
+                                *(__nv_bfloat16 *)(sm + SM_W1 + kmajor_off(j, k)) = __float2bfloat16_rn(wscale * w[v]);
                             }
                         }
                     }
@@ -454,6 +489,11 @@ __global__ void __launch_bounds__(NT, 1) k_tc_batched(TcArgs a) {
                 tc_fence_before();
                 if (!epi_sync()) { ok = false; break; }
                 mbar_arrive(BAR_W);
+                if (want_gn && half == 0 && r == 0) {
+                    double u = 0.0;
+                    for (int w = 0; w < NEPI; ++w) u += gnr[w];
+                    gnorm_hist[e] = sqrt(fma((double)gb2, (double)gb2, u));
+                }
             }
         }
         if (*abort && tid == 0) atomicOr(a.status, ST_TIMEOUT);
@@ -485,6 +525,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 }  // namespace
 
+static_assert(sizeof(TcNet) % 16 == 0, "descriptor stride");
 size_t tc_desc_bytes() { return sizeof(TcNet); }
 size_t tc_tmap_bytes() { return sizeof(CUtensorMap); }
 
@@ -506,26 +547,28 @@ cudaError_t tc_encode_map(void *map, const void *X, int D, int64_t n) {
 }
 
 // Fills the device-side descriptor (host image) of one net.
-void tc_fill_desc(void *desc, const void *tmap_dev, const float *y, float *params, double *loss_hist, int64_t n,
-                  int H) {
+void tc_fill_desc(void *desc, const void *tmap_dev, const float *y, float *params, double *loss_hist,
+                  double *gnorm_hist, int64_t n, int H) {
     TcNet *d = (TcNet *)desc;
     d->tmap = (const CUtensorMap *)tmap_dev;
     d->y = y;
     d->params = params;
     d->loss_hist = loss_hist;
+    d->gnorm_hist = gnorm_hist;
     d->n = n;
     d->H = H;
     d->pad = 0;
 }
 
 cudaError_t tc_batched_train(const void *descs_dev, const int *order_dev, int n_nets, int D, int epochs, float lr,
-                             int loss_mean, int *status, cudaStream_t st) {
+                             int loss_mean, int act, int *status, cudaStream_t st) {
     if (n_nets == 0 || epochs == 0) return cudaSuccess;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_tc_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM_ALLOC);
+    auto kern = act == MLP_ACT_TANH ? k_tc_batched<MLP_ACT_TANH> : k_tc_batched<MLP_ACT_SIGMOID>;
+    static bool attr_set[2] = {false, false};
+    if (!attr_set[act == MLP_ACT_TANH]) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM_ALLOC);
         if (e != cudaSuccess) return e;
-        attr_set = true;
+        attr_set[act == MLP_ACT_TANH] = true;
     }
     TcArgs a;
     a.nets = (const TcNet *)descs_dev;
@@ -535,9 +578,10 @@ cudaError_t tc_batched_train(const void *descs_dev, const int *order_dev, int n_
     a.epochs = epochs;
     a.lr = lr;
     a.loss_mean = loss_mean;
+    a.act = act;
     a.status = status;
     const int grid = n_nets < device_sm_count() ? n_nets : device_sm_count();
-    k_tc_batched<<<grid, NT, SM_ALLOC, st>>>(a);
+    kern<<<grid, NT, SM_ALLOC, st>>>(a);
     return cudaGetLastError();
 }
 

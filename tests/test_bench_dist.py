@@ -51,24 +51,38 @@ def test_traffic_records_follow_kernel_sources(tmp_path, monkeypatch):
     """The roofline's DRAM traffic comes from committed ncu summaries only while
     the kernel's sources still hash to the recorded value, and a record is
     picked by kernel and workload."""
+    import hashlib
+    import json
     import shutil
 
     import bench
-    assert bench.traffic_from_profile() is not None
-    c0 = bench.traffic_record("k_fused_train", bench.C0_WORKLOAD)
-    c1 = bench.traffic_record("k_fused_train", bench.WORKLOAD)
-    assert c0 is not None and c1 is not None and c0 != c1
-    assert bench.traffic_record("k_fused_train", "no such workload") is None
-    # a copy of the tree whose fused kernel source differs by one byte
     root = tmp_path / "tree"
-    shutil.copytree(os.path.join(bench.ROOT, "profiles"), root / "profiles")
     csrc = root / "paper_1908_07847_gb300" / "csrc"
     shutil.copytree(os.path.join(bench.ROOT, "paper_1908_07847_gb300", "csrc"), csrc)
+    (root / "profiles").mkdir()
+
+    def record(kernel, workload, sources, nbytes):
+        h = hashlib.sha256()
+        for f in sources:
+            h.update(open(csrc / f, "rb").read())
+        return "traffic-record: " + json.dumps({"kernel": kernel, "workload": workload, "sources": sources,
+                                                 "source_sha256_16": h.hexdigest()[:16],
+                                                 "dram_bytes_per_launch": nbytes})
+
+    src = ["fused_kernels.cu", "row_engine.cuh", "mlp_internal.cuh"]
+    (root / "profiles" / "a.md").write_text("\n".join([
+        "# summary", record("k_fused_train", "w1", src, 111), record("k_fused_train", "w2", src, 222),
+        record("k_batched_train", "w3", ["batched_kernels.cu", "row_engine.cuh"], 333)]) + "\n")
     monkeypatch.setattr(bench, "ROOT", str(root))
-    assert bench.traffic_record("k_fused_train", bench.WORKLOAD) is not None
+    assert bench.traffic_record("k_fused_train", "w1")["dram_bytes_per_launch"] == 111
+    assert bench.traffic_record("k_fused_train", "w2")["dram_bytes_per_launch"] == 222
+    assert bench.traffic_record("k_fused_train", "no such workload") is None
+    assert bench.traffic_record("k_batched_train")["dram_bytes_per_launch"] == 333
+    # the fused kernel's source changes by one byte: its records lapse, the
+    # other kernel's stays
     with open(csrc / "fused_kernels.cu", "a") as f:
         f.write("\n")
-    assert bench.traffic_record("k_fused_train", bench.WORKLOAD) is None
+    assert bench.traffic_record("k_fused_train", "w1") is None
     assert bench.traffic_record("k_batched_train") is not None
 
 
@@ -93,7 +107,7 @@ def test_reference_arm_prints_one_contract_line():
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
-    assert d["config"]["workload"] == bench.WORKLOAD
+    assert d["config"] == bench.c2_config(1)
 
 
 def test_reference_arm_under_torchrun_prints_once():

@@ -34,18 +34,20 @@ def unflat(p, H):
     return Params(p[:HD].reshape(H, D_PAD), p[HD:HD + H], p[HD + H:HD + 2 * H], p[-1])
 
 
-def run(X, y, W, epochs, lr, mb=0, loss_mean=1):
+def run(X, y, W, epochs, lr, mb=0, loss_mean=1, act=B.MLP_ACT_SIGMOID, norms=False):
     import torch
     H = W[0].shape[0]
-    with Net(D_PAD, H, lr, loss_mean, B.MLP_BF16) as net:
+    with Net(D_PAD, H, lr, loss_mean, B.MLP_BF16, act) as net:
         net.set(W)
         Xd = dev(I.bf16_bits(X).view(np.int16))
         yd = dev(y)
         L = torch.zeros(max(epochs, 1), dtype=torch.float64, device="cuda")
-        B.mlp_train_epochs(net.h, Xd, yd, X.shape[0], epochs, mb, L, None, stream())
+        G = torch.zeros(max(epochs, 1), dtype=torch.float64, device="cuda") if norms else None
+        B.mlp_train_epochs(net.h, Xd, yd, X.shape[0], epochs, mb, L, G, stream())
         st = net.check()
         assert st == B.MLP_OK, B.mlp_last_error()
-        return net.flat(), host(L)[:epochs]
+        out = net.flat(), host(L)[:epochs]
+        return out + (host(G)[:epochs],) if norms else out
 
 
 ONE_STEP = [(1, 256), (100, 256), (128, 512), (777, 768), (1000, 1024), (2500, 2048)]
@@ -178,3 +180,70 @@ def test_one_step_gradient_over_input_widths(D_real, D_pad):
     HD = H * D_pad
     assert rel_err_norm(g[HD:HD + H], ref[1]) <= BF16_GRAD_TOL, "gb1"
     assert np.all(got[:HD].reshape(H, D_pad)[:, D_real:] == 0.0)
+
+
+@pytest.mark.parametrize("mb", [0, 1000])
+def test_gradient_norm_matches_oracle(mb):
+    """gnorm_hist on the cluster kernel (full batch, and mini-batches whose
+    last one is ragged: the norm of each epoch's last update) within the bf16
+    gradient bar of the oracle's."""
+    n, H = 2600, 768
+    X, y, W = make(3900 + mb, n, H)
+    got, L, G = run(X, y, W, 3, lr32(), mb=mb, norms=True)
+    q, lh, gh = oracle.train(X, y, Params(*W), lr32(), 3, minibatch=mb)
+    assert rel_err_elem(G, gh) <= BF16_GRAD_TOL
+    assert rel_err_elem(L, lh) <= BF16_GRAD_TOL
+
+
+@pytest.mark.parametrize("n,H", [(300, 256), (1500, 1024)])
+def test_tanh_one_step_gradient(n, H):
+    """tanh hidden units (Sec. 2.2's other activation) on the cluster kernel:
+    one full-batch step at lr = 1 moves the weights by -g within the bf16 bar."""
+    X, y, W = make(4000 + n, n, H)
+    got, _ = run(X, y, W, 1, 1.0, act=B.MLP_ACT_TANH)
+    ref = oracle.mse_gradients(X, y, Params(*W), act=oracle.ACT_TANH)
+    exp = np.concatenate([ref[0].ravel(), ref[1], ref[2], [ref[3]]])
+    g = flat(W) - got
+    assert rel_err_norm(g, exp) <= BF16_GRAD_TOL
+    HD = H * D_PAD
+    assert rel_err_norm(g[HD:HD + H], ref[1]) <= BF16_GRAD_TOL, "gb1"
+    assert rel_err_norm(g[HD + H:HD + 2 * H], ref[2]) <= BF16_GRAD_TOL, "gw2"
+
+
+def test_tanh_minibatch_training_accuracy():
+    n, H, mb, epochs = 4000, 512, 1024, 4
+    X, y, W = make(4100, n, H)
+    got, L = run(X, y, W, epochs, lr32(), mb=mb, act=B.MLP_ACT_TANH)
+    q, lh, _ = oracle.train(X, y, Params(*W), lr32(), epochs, minibatch=mb, act=oracle.ACT_TANH)
+    assert rel_err_elem(L, lh) <= BF16_GRAD_TOL
+    acc_gpu = (oracle.predict(X, unflat(got, H), act=oracle.ACT_TANH) == y).mean()
+    acc_ref = (oracle.predict(X, q, act=oracle.ACT_TANH) == y).mean()
+    assert abs(acc_gpu - acc_ref) <= 0.01
+
+
+def test_wide_net_20_epochs_against_stored_oracle_run():
+    """The wide workload's whole schedule on its first 65,536 rows: 48-2048-1,
+    the first 49,152 rows (75 %) trained by mini-batches of 8192 for 20 epochs
+    (120 updates), against the oracle's run of the same schedule
+    (tests/golden/c3_wide_net_20epochs.json): train and test accuracy within
+    one point, loss and gradient-norm histories within 2e-2, and the stored
+    weights' change within 2e-2 (max-norm relative)."""
+    import json
+    import os
+    from tests import bf16_workloads as WL
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "c3_wide_net_20epochs.json")))
+    X = WL.c3_rows()
+    y = labels_from_teacher(X, D_REAL)
+    W = WL.c3_weights()
+    ntr = WL.C3_TRAIN
+    got, L, G = run(X[:ntr], y[:ntr], W, WL.C3_EPOCHS, lr32(), mb=WL.C3_MB, norms=True)
+    pg = unflat(got, WL.C3_H)
+    acc_tr = (oracle.predict(X[:ntr], pg) == y[:ntr]).mean()
+    acc_te = (oracle.predict(X[ntr:], pg) == y[ntr:]).mean()
+    assert abs(acc_tr - gold["train_acc"]) <= 0.01, (acc_tr, gold["train_acc"])
+    assert abs(acc_te - gold["test_acc"]) <= 0.01, (acc_te, gold["test_acc"])
+    assert rel_err_elem(L, gold["loss_hist"]) <= BF16_GRAD_TOL
+    assert rel_err_elem(G, gold["gnorm_hist"]) <= BF16_GRAD_TOL
+    w0 = WL.kept_params(*W, WL.C3_KEEP_EVERY)
+    w = WL.kept_params(pg.W1, pg.b1, pg.w2, pg.b2, WL.C3_KEEP_EVERY)
+    assert rel_err_norm(w - w0, np.asarray(gold["kept_params"]) - w0) <= BF16_GRAD_TOL
