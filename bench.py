@@ -570,7 +570,8 @@ def c2_workload():
 C2_WORKLOAD = c2_workload()
 
 
-KERNEL_OF_SHAPE = {0: "k_batched_train", 1: "k_batched_train2", 2: "k_batched_train2"}
+KERNEL_OF_SHAPE = {0: "k_batched_train", 1: "k_batched_train2", 2: "k_batched_train2", 3: "k_batched_tiled",
+                   4: "k_batched_tiled", 5: "k_batched_tiled"}
 
 
 def c2_shapes(world: int):

@@ -147,6 +147,14 @@ mlp_status mlp_train_epochs(mlp_t net, const void *X, const void *y, int64_t n,
                             int32_t epochs, int64_t minibatch, double *loss_hist,
                             double *gnorm_hist, void *stream);
 
+/* Which path mlp_train_epochs takes for this handle and these sizes, so that
+ * a caller can tell a shape that leaves the fast kernels (the plain path runs
+ * several kernels a step and is about 10x slower) before training:
+ * MLP_PATH_FUSED (the fused FP32 kernel), MLP_PATH_TC_CLUSTER (the bf16
+ * tensor-core cluster kernel) or MLP_PATH_PLAIN.  No device work. */
+typedef enum { MLP_PATH_FUSED = 0, MLP_PATH_TC_CLUSTER = 1, MLP_PATH_PLAIN = 2 } mlp_path;
+mlp_status mlp_train_path(mlp_t net, int64_t n, int64_t minibatch, int32_t *path);
+
 /* mlp_train_epochs on host buffers: copies X and y to device staging memory
  * owned by the handle, trains, and copies the loss history back to
  * loss_hist_host (may be NULL).  Synchronous.  A one-epoch call that takes the
@@ -254,7 +262,12 @@ mlp_status mlp_batch_check(mlp_batch_t b, void *stream);
  *   1  two hidden units a lane (each row word read from shared memory feeds
  *      two multiply-adds), blocks of 4 warps, two per SM, one row in flight
  *      per lane (D <= 36);
- *   2  as 1 with two rows in flight per lane (D = 33, the paper's markers).
+ *   2  as 1 with two rows in flight per lane (D = 33, the paper's markers);
+ *   3  register-tiled products (each thread a 4 x 4 tile of the forward and
+ *      of the weight gradient, all sums in registers), blocks of 4 warps,
+ *      rows in chunks of up to 128 (D <= 36);
+ *   4  as 3 with chunks of 64 rows (less shared memory, more blocks an SM);
+ *   5  as 3 with chunks of 32 rows.
  * A new FP32 plan has shape 0.  set: MLP_EINVAL for a shape the plan's D
  * does not take, MLP_EUNSUPPORTED for a BF16 plan.  get: -1 for BF16 plans. */
 mlp_status mlp_batch_set_shape(mlp_batch_t b, int32_t shape);

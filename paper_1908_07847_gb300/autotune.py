@@ -4,9 +4,11 @@
   each step's rows over blocks; more blocks shorten the row phase but add
   cross-block traffic and barrier participants.
 * ``tune_batched``: the kernel shape of an FP32 many-nets plan
-  (mlp_batch_set_shape): one hidden unit a lane in blocks of 8 warps, or two
-  units a lane in blocks of 4 warps with one or two rows in flight.  Which is
-  fastest depends on the plan's mix of widths and row counts.
+  (mlp_batch_set_shape): one hidden unit a lane in blocks of 8 warps; two
+  units a lane in blocks of 4 warps with one or two rows in flight; or
+  register-tiled products over row chunks of 128, 64 or 32 rows (which trade
+  shared memory for blocks an SM).  Which is fastest depends on the plan's mix
+  of widths and row counts.
 
 Each times its candidates on the caller's device and workload and caches the
 fastest in a JSON file (``$MLP_GB300_TUNE_CACHE``, else
@@ -103,7 +105,7 @@ def configure(handle, X, y, D, H, n, minibatch=0, act=B.MLP_ACT_SIGMOID):
     return rows
 
 
-BATCH_SHAPES = (0, 1, 2)
+BATCH_SHAPES = (0, 1, 2, 3, 4, 5)
 
 
 def _batch_key(device_name, D, Hs, ns, act):

@@ -14,6 +14,7 @@ import threading
 MLP_OK, MLP_EINVAL, MLP_ENOMEM, MLP_ECUDA, MLP_ETIMEOUT, MLP_ENONFINITE, MLP_EUNSUPPORTED = range(7)
 MLP_FP32, MLP_BF16, MLP_FP64 = 0, 1, 2
 MLP_ACT_SIGMOID, MLP_ACT_TANH = 0, 1
+MLP_PATH_FUSED, MLP_PATH_TC_CLUSTER, MLP_PATH_PLAIN = 0, 1, 2
 STATUS_NAMES = {0: "MLP_OK", 1: "MLP_EINVAL", 2: "MLP_ENOMEM", 3: "MLP_ECUDA", 4: "MLP_ETIMEOUT",
                 5: "MLP_ENONFINITE", 6: "MLP_EUNSUPPORTED"}
 
@@ -23,7 +24,7 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "lib
 EXPORTS = [
     "mlp_create", "mlp_destroy", "mlp_set_weights", "mlp_get_weights", "mlp_weights_device",
     "mlp_forward", "mlp_backward", "mlp_update", "mlp_step_plain", "mlp_train_epochs",
-    "mlp_train_host", "mlp_predict", "mlp_check", "mlp_workspace_bytes", "mlp_forward_w",
+    "mlp_train_host", "mlp_train_path", "mlp_predict", "mlp_check", "mlp_workspace_bytes", "mlp_forward_w",
     "mlp_backward_w", "mlp_debug_skip_block", "mlp_set_rows_per_block", "mlp_batch_train",
     "mlp_batch_create", "mlp_batch_run", "mlp_batch_check", "mlp_batch_destroy", "mlp_batch_create_host",
     "mlp_batch_run_host", "mlp_batch_set_shape", "mlp_batch_get_shape", "mlp_train_fused_noalloc",
@@ -79,6 +80,7 @@ def lib():
             "mlp_step_plain": (S, [V, V, V, I64, V, V]),
             "mlp_train_epochs": (S, [V, V, V, I64, I32, I64, V, V, V]),
             "mlp_train_host": (S, [V, V, V, I64, I32, I64, V, V]),
+            "mlp_train_path": (S, [V, I64, I64, ctypes.POINTER(I32)]),
             "mlp_predict": (S, [V, V, I64, V, V]),
             "mlp_check": (S, [V, V]),
             "mlp_workspace_bytes": (S, [I32, I32, I32, I64, ctypes.POINTER(U64)]),
@@ -185,6 +187,14 @@ def mlp_train_epochs(h, X, y, n, epochs, minibatch=0, loss_hist=None, gnorm_hist
 
 def mlp_train_host(h, X_host, y_host, n, epochs, minibatch=0, loss_hist_host=None, stream=0):
     return _ck(lib().mlp_train_host(h, _p(X_host), _p(y_host), n, epochs, minibatch, _p(loss_hist_host), stream))
+
+
+def mlp_train_path(h, n, minibatch=0):
+    """MLP_PATH_FUSED, MLP_PATH_TC_CLUSTER or MLP_PATH_PLAIN: the path
+    mlp_train_epochs takes for this handle and size."""
+    v = ctypes.c_int32()
+    _ck(lib().mlp_train_path(h, n, minibatch, ctypes.byref(v)))
+    return v.value
 
 
 def mlp_predict(h, X, n, labels, stream=0):

@@ -399,6 +399,17 @@ mlp_status mlp_train_epochs(mlp_t h, const void *X, const void *y, int64_t n, in
     return MLP_OK;
 }
 
+mlp_status mlp_train_path(mlp_t h, int64_t n, int64_t minibatch, int32_t *path) {
+    if (check_handle(h)) return MLP_EINVAL;
+    if (!path || n < 0) return fail(MLP_EINVAL, "mlp_train_path: bad arguments");
+    (void)minibatch;   // every path takes any mini-batch size
+    const int D = h->cfg.D, H = h->cfg.H;
+    if (h->cfg.prec == MLP_FP32 && mlp::fused_supported(D, H)) *path = MLP_PATH_FUSED;
+    else if (h->cfg.prec == MLP_BF16 && mlp::tc_cluster_supported(D, H)) *path = MLP_PATH_TC_CLUSTER;
+    else *path = MLP_PATH_PLAIN;
+    return MLP_OK;
+}
+
 mlp_status mlp_train_host(mlp_t h, const void *X_host, const void *y_host, int64_t n, int32_t epochs,
                           int64_t minibatch, double *loss_hist_host, void *stream) {
     if (check_handle(h)) return MLP_EINVAL;
@@ -565,6 +576,7 @@ struct mlp_batch {
     size_t x_bytes = 0, y_bytes = 0, p_bytes = 0;
     int max_epochs = 0;
     int shape = mlp::BATCH_SHAPE_U1;   // FP32 kernel shape (mlp_batch_set_shape)
+    int64_t nmax = 0;                   // FP32: the most rows of any net
 };
 
 // BF16 plan: per-net TMA tensor maps and descriptors for the tcgen05 kernel.
@@ -656,6 +668,7 @@ mlp_status mlp_batch_create(int32_t prec, int32_t act, int32_t D, const mlp_net_
     if (prec == MLP_BF16) return batch_create_tc(act, D, nets, n_nets, lr, loss_mean, out);
     if (D < 1 || D > mlp::batched_max_D()) return fail(MLP_EINVAL, "mlp_batch_create: D=%d out of 1..64", D);
     int Hmax = 1;
+    int64_t nmax = 0;
     std::vector<mlp::BatchNet> host(n_nets);
     std::vector<double> cost(n_nets);
     for (int t = 0; t < n_nets; ++t) {
@@ -665,6 +678,7 @@ mlp_status mlp_batch_create(int32_t prec, int32_t act, int32_t D, const mlp_net_
         if (d.n < 0 || !d.params || (d.n > 0 && (!d.X || !d.y)))
             return fail(MLP_EINVAL, "mlp_batch_create: net %d has a null buffer or n < 0", t);
         Hmax = d.H > Hmax ? d.H : Hmax;
+        nmax = d.n > nmax ? d.n : nmax;
         host[t] = {(const float *)d.X, d.y, d.params, d.loss_hist, d.gnorm_hist, d.n, d.H, 0};
         // lanes busy per row: a power-of-two segment up to 32, else 32 per 32 units
         int lanes = d.H <= 32 ? 4 : 32 * ((d.H + 31) / 32);
@@ -685,6 +699,7 @@ mlp_status mlp_batch_create(int32_t prec, int32_t act, int32_t D, const mlp_net_
     b->act = act;
     b->D = D;
     b->Hmax = Hmax;
+    b->nmax = nmax;
     b->n_nets = n_nets;
     b->lr = lr;
     b->loss_mean = loss_mean ? 1 : 0;
@@ -725,8 +740,8 @@ mlp_status mlp_batch_run(mlp_batch_t b, int32_t epochs, void *stream) {
            "tensor-core batched training kernel");
         return MLP_OK;
     }
-    CK(mlp::batched_train(b->act, b->D, b->Hmax, b->nets, b->order, b->n_nets, epochs, b->lr, b->loss_mean,
-                          b->status, b->shape, (cudaStream_t)stream),
+    CK(mlp::batched_train(b->act, b->D, b->Hmax, b->nmax, b->nets, b->order, b->n_nets, epochs, b->lr,
+                          b->loss_mean, b->status, b->shape, (cudaStream_t)stream),
        "batched training kernel");
     return MLP_OK;
 }

@@ -149,6 +149,8 @@ bool batched_shape_supported(int D, int shape) {
     if (shape == BATCH_SHAPE_U1) return dp_for(D) != 0;
     if (shape == BATCH_SHAPE_U2_RB1) return batched_u2_supported(D, 1);
     if (shape == BATCH_SHAPE_U2_RB2) return batched_u2_supported(D, 2);
+    if (shape == BATCH_SHAPE_TILED128 || shape == BATCH_SHAPE_TILED64 || shape == BATCH_SHAPE_TILED32)
+        return batched_tiled_supported(D, 128);
     return false;
 }
 
@@ -164,8 +166,11 @@ void batched_smem_layout(int D, int Hmax, int *part_floats, int *wm_floats, size
     *bytes = sizeof(float) * ((size_t)BCAP * DP + BCAP + wm + pf + RE_ZX);
 }
 
-cudaError_t batched_train(int act, int D, int Hmax, const BatchNet *nets_dev, const int *order_dev, int n_nets,
-                          int epochs, float lr, int loss_mean, int *status, int shape, cudaStream_t st) {
+cudaError_t batched_train(int act, int D, int Hmax, int64_t nmax, const BatchNet *nets_dev, const int *order_dev,
+                          int n_nets, int epochs, float lr, int loss_mean, int *status, int shape, cudaStream_t st) {
+    if (shape == BATCH_SHAPE_TILED128 || shape == BATCH_SHAPE_TILED64 || shape == BATCH_SHAPE_TILED32)
+        return batched_train_tiled(act, D, Hmax, nmax, nets_dev, order_dev, n_nets, epochs, lr, loss_mean, status,
+                                   shape == BATCH_SHAPE_TILED32 ? 32 : (shape == BATCH_SHAPE_TILED64 ? 64 : 128), st);
     if (shape != BATCH_SHAPE_U1)
         return batched_train_u2(act, D, Hmax, nets_dev, order_dev, n_nets, epochs, lr, loss_mean, status,
                                 shape == BATCH_SHAPE_U2_RB2 ? 2 : 1, st);

@@ -1,0 +1,351 @@
+// Many independent networks in one launch, each net's epoch computed as two
+// small register-tiled products (inputs up to 36 wide).  The method per net is
+// the one of batched_kernels.cu (Sec. 2.2 of arXiv 1908.07847: feed-forward,
+// output error, backpropagation, full-batch gradient descent without
+// momentum); only the schedule differs.  Per chunk of up to `ncap` rows:
+//
+//   1. Z = [X | 1] [W1 | b1]^T, every thread a 4-row x 4-unit tile of Z with
+//      its 16 sums in registers (one 16-byte word of X^T and one of W^T a
+//      step: 16 multiply-adds per two shared-memory loads); h = f(Z) goes to
+//      shared memory;
+//   2. one thread a row: z2 = b2 + h w2, o = sigmoid(z2), d2 = c (o - y) o (1 - o);
+//   3. d1 = d2 w2 f'(h) written over h, and the row subsets' partial
+//      gw2 = sum_rows h d2, in registers;
+//   4. [gW1 | gb1] += d1^T [X | 1], every thread up to three 4-unit x 4-input
+//      tiles held in registers across the chunks (per 4 rows: 8 loads, 64
+//      multiply-adds).
+// At the end of the epoch each thread applies its own tiles' update to the
+// transposed weights in shared memory; gw2, gb2, the loss and the gradient
+// norm are summed in fixed orders.  Every sum has one fixed order, so a run
+// is bitwise reproducible.  X^T (ncap columns), W^T, and h / d1 (ncap rows)
+// live in shared memory; padding rows of X^T and padding units of W^T and w2
+// are zero, so their d1 and their share of z2 are zero and they add nothing.
+// Nets with more than ncap rows stream their rows in chunks.
+#include "mlp_internal.cuh"
+
+namespace mlp {
+
+namespace {
+
+constexpr int TNT = 128;          // threads per block
+constexpr int TSLOTS = 3;         // gradient tiles a thread holds (<= 32 x 10 tiles)
+
+struct TLayout {
+    int K;       // D + 1 (the ones column carries the bias)
+    int KQ;      // K rounded up to 4, / 4
+    int ncap;    // rows per chunk (multiple of 4)
+    int HP;      // Hmax rounded up to 4
+    int HSS;     // row stride of h / d1 (HP + 4: rows fall in different banks)
+    // float offsets
+    int xt, wt, hs, w2, d2, gwp, red;
+    int total;
+};
+
+__host__ __device__ inline TLayout t_layout(int D, int Hmax, int ncap) {
+    TLayout L;
+    L.K = D + 1;
+    L.KQ = (L.K + 3) / 4;
+    L.ncap = ncap;
+    L.HP = (Hmax + 3) & ~3;
+    L.HSS = L.HP + 4;
+    L.xt = 0;                                   // X^T: 4 KQ rows x ncap
+    L.wt = L.xt + 4 * L.KQ * ncap;              // W^T: 4 KQ rows x HP
+    L.hs = L.wt + 4 * L.KQ * L.HP;              // h / d1: ncap x HSS
+    L.w2 = L.hs + ncap * L.HSS;                 // w2: HP
+    L.d2 = L.w2 + L.HP;                         // d2: ncap
+    L.gwp = L.d2 + ncap;                        // gw2 partials: TNT x 4
+    L.red = L.gwp + 4 * TNT;                    // reductions: 4 warps x (sse, gb2) + 4 doubles
+    L.total = L.red + 32;
+    return L;
+}
+
+template <int ACT>
+__device__ __forceinline__ float dact(float h) { return Act<ACT>::df(h); }
+
+template <int ACT>
+__device__ __forceinline__ void net_tiled(const BatchNet &nd, int D, int epochs, float lr, int loss_mean,
+                                          int *status, float *sm, const TLayout &L) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int H = nd.H, K = L.K, HQ = (H + 3) / 4, HP = L.HP;
+    const int64_t n = nd.n;
+    float *XT = sm + L.xt, *WT = sm + L.wt, *HS = sm + L.hs, *w2s = sm + L.w2, *d2s = sm + L.d2;
+    float *gwp = sm + L.gwp, *red = sm + L.red;
+    double *redd = (double *)(red + 16);
+    const float *P = nd.params;
+    const int HD = H * D;
+
+    // W^T (row k < D: W1[., k]; row D: b1; rows above and units >= H: 0), w2
+    for (int i = tid; i < 4 * L.KQ * HP; i += TNT) {
+        const int k = i / HP, j = i - k * HP;
+        float v = 0.f;
+        if (j < H) v = k < D ? P[j * D + k] : (k == D ? P[HD + j] : 0.f);
+        WT[i] = v;
+    }
+    for (int j = tid; j < HP; j += TNT) w2s[j] = j < H ? P[HD + H + j] : 0.f;
+    float b2 = P[HD + 2 * H];
+    // X^T of rows r0 .. r0 + nc - 1 (row D: ones; padding rows and columns 0)
+    auto load_chunk = [&](int64_t r0, int nc) {
+        const int cols = L.ncap;
+        for (int i = tid; i < 4 * L.KQ * cols; i += TNT) {
+            const int k = i / cols, r = i - k * cols;
+            float v = 0.f;
+            if (r < nc) v = k < D ? nd.X[(r0 + r) * D + k] : (k == D ? 1.f : 0.f);
+            XT[i] = v;
+        }
+    };
+    const bool resident = n <= L.ncap;
+    if (resident) load_chunk(0, (int)n);
+    __syncthreads();
+    const float c = loss_mean ? 1.0f / (float)n : 1.0f;
+    const double C = loss_mean ? 1.0 / (double)n : 1.0;
+    const bool want_gn = nd.gnorm_hist != nullptr;
+    const int KQ = L.KQ;
+    const int T2 = HQ * KQ;             // gradient tiles (4 units x 4 inputs)
+    const int RS = TNT / HQ;            // row subsets of step 3
+    const int uq3 = tid % HQ, rs3 = tid / HQ;
+
+    for (int e = 0; e < epochs; ++e) {
+        float g[TSLOTS][4][4];
+#pragma unroll
+        for (int s = 0; s < TSLOTS; ++s)
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) g[s][u][k] = 0.f;
+        float gw2a[4] = {0.f, 0.f, 0.f, 0.f};
+        float sse_f = 0.f, gb2_f = 0.f;
+
+        for (int64_t r0 = 0; r0 < n; r0 += L.ncap) {
+            const int nc = (int)min((int64_t)L.ncap, n - r0);
+            const int nc4 = (nc + 3) & ~3;
+            if (!resident) {
+                __syncthreads();
+                load_chunk(r0, nc);
+                __syncthreads();
+            }
+            // ---- 1. Z = [X | 1] [W1 | b1]^T by 4 x 4 tiles, h = f(Z)
+            const int T1 = (nc4 / 4) * HQ;
+            for (int t = tid; t < T1; t += TNT) {
+                const int rq = t / HQ, uq = t - rq * HQ;
+                float z[4][4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) z[i][u] = 0.f;
+                const float *xa = XT + 4 * rq, *wb = WT + 4 * uq;
+#pragma unroll 2
+                for (int k = 0; k < K; ++k) {
+                    const float4 a = *reinterpret_cast<const float4 *>(xa + k * L.ncap);
+                    const float4 b = *reinterpret_cast<const float4 *>(wb + k * HP);
+                    const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) z[i][u] = fmaf(av[i], bv[u], z[i][u]);
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    *reinterpret_cast<float4 *>(HS + (4 * rq + i) * L.HSS + 4 * uq) =
+                        make_float4(Act<ACT>::f(z[i][0]), Act<ACT>::f(z[i][1]), Act<ACT>::f(z[i][2]),
+                                    Act<ACT>::f(z[i][3]));
+            }
+            __syncthreads();
+            // ---- 2. one thread a row: z2, o, d2 (rows nc .. nc4 - 1 get d2 = 0)
+            for (int r = tid; r < nc4; r += TNT) {
+                float d2 = 0.f;
+                if (r < nc) {
+                    const float *hr = HS + r * L.HSS;
+                    float za = 0.f, zb = 0.f;
+                    for (int q = 0; q < HQ; ++q) {
+                        const float4 h4 = *reinterpret_cast<const float4 *>(hr + 4 * q);
+                        const float4 w4 = *reinterpret_cast<const float4 *>(w2s + 4 * q);
+                        za = fmaf(h4.x, w4.x, za);
+                        zb = fmaf(h4.y, w4.y, zb);
+                        za = fmaf(h4.z, w4.z, za);
+                        zb = fmaf(h4.w, w4.w, zb);
+                    }
+                    const float o = sigmoid_out((za + zb) + b2);
+                    const float err = o - nd.y[r0 + r];
+                    d2 = c * err * o * (1.0f - o);
+                    sse_f = fmaf(err, err, sse_f);
+                    gb2_f += d2;
+                }
+                d2s[r] = d2;
+            }
+            __syncthreads();
+            // ---- 3. d1 = d2 w2 f'(h) over h; partial gw2 = sum h d2 per row subset
+            if (rs3 < RS) {
+                const float4 w4 = *reinterpret_cast<const float4 *>(w2s + 4 * uq3);
+                for (int r = rs3; r < nc4; r += RS) {
+                    float *hp = HS + r * L.HSS + 4 * uq3;
+                    const float4 h4 = *reinterpret_cast<const float4 *>(hp);
+                    const float d2 = d2s[r];
+                    gw2a[0] = fmaf(h4.x, d2, gw2a[0]);
+                    gw2a[1] = fmaf(h4.y, d2, gw2a[1]);
+                    gw2a[2] = fmaf(h4.z, d2, gw2a[2]);
+                    gw2a[3] = fmaf(h4.w, d2, gw2a[3]);
+                    *reinterpret_cast<float4 *>(hp) =
+                        make_float4(d2 * w4.x * dact<ACT>(h4.x), d2 * w4.y * dact<ACT>(h4.y),
+                                    d2 * w4.z * dact<ACT>(h4.z), d2 * w4.w * dact<ACT>(h4.w));
+                }
+            }
+            __syncthreads();
+            // ---- 4. [gW1 | gb1] += d1^T [X | 1], 4 rows at a time
+#pragma unroll
+            for (int s = 0; s < TSLOTS; ++s) {
+                const int t = tid + s * TNT;
+                if (t < T2) {
+                    const int kq = t / HQ, uq = t - kq * HQ;
+                    const float *da = HS + 4 * uq;
+                    const float *xb = XT + 4 * kq * L.ncap;
+                    for (int rr = 0; rr < nc4; rr += 4) {
+                        float4 dv[4], xv[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) dv[i] = *reinterpret_cast<const float4 *>(da + (rr + i) * L.HSS);
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) xv[k] = *reinterpret_cast<const float4 *>(xb + k * L.ncap + rr);
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const float d[4] = {dv[i].x, dv[i].y, dv[i].z, dv[i].w};
+                            const float xr[4] = {i == 0 ? xv[0].x : i == 1 ? xv[0].y : i == 2 ? xv[0].z : xv[0].w,
+                                                 i == 0 ? xv[1].x : i == 1 ? xv[1].y : i == 2 ? xv[1].z : xv[1].w,
+                                                 i == 0 ? xv[2].x : i == 1 ? xv[2].y : i == 2 ? xv[2].z : xv[2].w,
+                                                 i == 0 ? xv[3].x : i == 1 ? xv[3].y : i == 2 ? xv[3].z : xv[3].w};
+#pragma unroll
+                            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                                for (int k = 0; k < 4; ++k) g[s][u][k] = fmaf(d[u], xr[k], g[s][u][k]);
+                        }
+                    }
+                }
+            }
+            if (!resident) __syncthreads();   // the next chunk overwrites X^T and h
+        }
+
+        // ---- end of epoch: reductions in fixed orders, then the update
+        if (rs3 < RS) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) gwp[rs3 * 4 * HQ + 4 * uq3 + u] = gw2a[u];
+        }
+        sse_f = warp_sum(sse_f);
+        gb2_f = warp_sum(gb2_f);
+        if (lane == 0) {
+            red[2 * warp] = sse_f;
+            red[2 * warp + 1] = gb2_f;
+        }
+        __syncthreads();
+        float gb2 = 0.f;
+        double sse = 0.0;
+        for (int w = 0; w < TNT / 32; ++w) {
+            sse += (double)red[2 * w];
+            gb2 += red[2 * w + 1];
+        }
+        double gn = 0.0;
+        // gw2 (rows subsets in order) and the w2 / b2 update
+        for (int j = tid; j < H; j += TNT) {
+            float v = 0.f;
+            for (int q = 0; q < RS; ++q) v += gwp[q * 4 * HQ + j];
+            w2s[j] -= lr * v;
+            if (want_gn) gn = fma((double)v, (double)v, gn);
+        }
+        b2 -= lr * gb2;
+        // this thread's tiles of [gW1 | gb1] update W^T (row D of W^T is b1)
+#pragma unroll
+        for (int s = 0; s < TSLOTS; ++s) {
+            const int t = tid + s * TNT;
+            if (t < T2) {
+                const int kq = t / HQ, uq = t - kq * HQ;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int kk = 4 * kq + k;
+                    if (kk < K) {
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int j = 4 * uq + u;
+                            if (j < H) {
+                                WT[kk * HP + j] -= lr * g[s][u][k];
+                                if (want_gn) gn = fma((double)g[s][u][k], (double)g[s][u][k], gn);
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        if (want_gn) {
+            gn = warp_sum(gn);
+            if (lane == 0) redd[warp] = gn;
+        }
+        if (tid == 0) {
+            const double Lv = 0.5 * C * sse;
+            if (nd.loss_hist) nd.loss_hist[e] = Lv;
+            if (!isfinite(Lv)) atomicOr(status, ST_NONFINITE);
+        }
+        __syncthreads();
+        if (want_gn && tid == 0) {
+            double u = 0.0;
+            for (int w = 0; w < TNT / 32; ++w) u += redd[w];
+            nd.gnorm_hist[e] = sqrt(fma((double)gb2, (double)gb2, u));
+        }
+    }
+    // write the trained weights back in the packed layout
+    float *Pw = nd.params;
+    for (int i = tid; i < HD; i += TNT) {
+        const int j = i / D, k = i - j * D;
+        Pw[i] = WT[k * HP + j];
+    }
+    for (int j = tid; j < H; j += TNT) {
+        Pw[HD + j] = WT[D * HP + j];
+        Pw[HD + H + j] = w2s[j];
+    }
+    if (tid == 0) Pw[HD + 2 * H] = b2;
+    __syncthreads();
+}
+
+template <int ACT>
+__global__ void __launch_bounds__(TNT) k_batched_tiled(const BatchNet *__restrict__ nets, const int *__restrict__ order,
+                                                       int n_nets, int D, int Hmax, int ncap, int epochs, float lr,
+                                                       int loss_mean, int *status) {
+    extern __shared__ __align__(16) float smem[];
+    const TLayout L = t_layout(D, Hmax, ncap);
+    // every region is written before it is read (padding rows and units of
+    // h hold finite values whose d1, and whose weight in z2, are 0)
+    for (int i = threadIdx.x; i < L.total; i += TNT) smem[i] = 0.f;
+    __syncthreads();
+    for (int idx = blockIdx.x; idx < n_nets; idx += gridDim.x) {
+        const BatchNet nd = nets[order ? order[idx] : idx];
+        if (nd.n <= 0 || nd.H <= 0) {
+            if (threadIdx.x == 0)
+                for (int e = 0; e < epochs; ++e) {
+                    if (nd.loss_hist) nd.loss_hist[e] = 0.0;
+                    if (nd.gnorm_hist) nd.gnorm_hist[e] = 0.0;
+                }
+            continue;
+        }
+        net_tiled<ACT>(nd, D, epochs, lr, loss_mean, status, smem, L);
+    }
+}
+
+}  // namespace
+
+bool batched_tiled_supported(int D, int Hmax) { return D >= 1 && D <= 36 && Hmax >= 1 && Hmax <= 128; }
+
+size_t batched_tiled_smem(int D, int Hmax, int ncap) { return sizeof(float) * (size_t)t_layout(D, Hmax, ncap).total; }
+
+cudaError_t batched_train_tiled(int act, int D, int Hmax, int64_t nmax, const BatchNet *nets_dev,
+                                const int *order_dev, int n_nets, int epochs, float lr, int loss_mean, int *status,
+                                int ncap_max, cudaStream_t st) {
+    if (!batched_tiled_supported(D, Hmax)) return cudaErrorInvalidValue;
+    if (n_nets == 0 || epochs == 0) return cudaSuccess;
+    int ncap = (int)((nmax + 3) & ~(int64_t)3);
+    if (ncap > ncap_max) ncap = ncap_max;
+    if (ncap < 4) ncap = 4;
+    const size_t smem = batched_tiled_smem(D, Hmax, ncap);
+    void *fn = act == MLP_ACT_TANH ? (void *)k_batched_tiled<MLP_ACT_TANH> : (void *)k_batched_tiled<MLP_ACT_SIGMOID>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    void *args[] = {(void *)&nets_dev, (void *)&order_dev, (void *)&n_nets, (void *)&D, (void *)&Hmax,
+                    (void *)&ncap, (void *)&epochs, (void *)&lr, (void *)&loss_mean, (void *)&status};
+    return cudaLaunchKernel(fn, dim3((unsigned)n_nets), dim3(TNT), args, smem, st);
+}
+
+}  // namespace mlp

@@ -213,10 +213,11 @@ def test_empty_net_and_validation():
     assert e.value.status == B.MLP_EINVAL
 
 
-@pytest.mark.parametrize("shape", [1, 2])
-def test_two_units_a_lane_shapes_match_oracle(shape):
-    """The two-units-a-lane kernel shapes over every width edge (segments of
-    2..32 lanes, one and two warps a row) and row counts up to streamed ones,
+@pytest.mark.parametrize("shape", [1, 2, 3, 4, 5])
+def test_kernel_shapes_match_oracle(shape):
+    """The other kernel shapes (two units a lane: segments of 2..32 lanes, one
+    and two warps a row; register-tiled: 4 x 4 tiles over row chunks of 128,
+    64 or 32 rows) over every width edge and row counts up to streamed ones,
     sigmoid and tanh, against the oracle at the FP32 bars."""
     rng = np.random.default_rng(2)
     Hs = EDGE_H + [2] + list(rng.integers(1, 129, 8))
@@ -234,12 +235,13 @@ def test_two_units_a_lane_shapes_match_oracle(shape):
         assert rel_err_norm(got[t], ref[t].flat()) <= W_TOL, ("tanh", shape, t)
 
 
-@pytest.mark.parametrize("D", [5, 8, 16, 20, 32, 35, 36])
-def test_two_units_a_lane_input_width_classes(D):
+@pytest.mark.parametrize("shape", [1, 3])
+@pytest.mark.parametrize("D", [1, 5, 8, 16, 20, 32, 35, 36])
+def test_input_width_classes_of_the_other_shapes(D, shape):
     """Every input-width class of the two-units-a-lane shape (zero-padded
-    row buffers for D below the class width)."""
+    row buffers for D below the class width) and of the tiled shape."""
     nets = make_batch(14 + D, [3, 40, 100], [50, 129, 90], D=D)
-    got, _ = run_batch(nets, 12, D=D, shape=1)
+    got, _ = run_batch(nets, 12, D=D, shape=shape)
     ref, _ = oracle.batch_train([(X, y, Params(*W)) for X, y, W in nets], lr32(), 12, threads=3)
     for t in range(3):
         assert rel_err_norm(got[t], ref[t].flat()) <= W_TOL, (D, t)
@@ -269,7 +271,7 @@ def test_shape_validation_and_autotuner(tmp_path, monkeypatch):
     try:
         assert B.mlp_batch_get_shape(b) == 0
         shape, times = autotune.tune_batched(b, 33, Hs, ns, P, epochs=5, reps=1)
-        assert set(times) == {0, 1, 2} and shape in times and B.mlp_batch_get_shape(b) == shape
+        assert set(times) == {0, 1, 2, 3, 4, 5} and shape in times and B.mlp_batch_get_shape(b) == shape
         assert torch.equal(P, P0)                       # the tuner's launches were undone
         again, _ = autotune.tune_batched(b, 33, Hs, ns, P, epochs=5, reps=1)   # from the cache
         assert again == shape and torch.equal(P, P0)
@@ -289,7 +291,7 @@ def test_shape_validation_and_autotuner(tmp_path, monkeypatch):
     b = B.mlp_batch_create(B.MLP_FP32, 0, 40, [B.mlp_net_desc(10, 40, Xd.data_ptr(), yd.data_ptr(), Pn.data_ptr(),
                                                               None)], lr32(), 1)
     try:
-        for bad in (1, 2, 3, -1):
+        for bad in (1, 2, 3, 4, 5, 6, -1):
             with pytest.raises(B.MLPError) as e:
                 B.mlp_batch_set_shape(b, bad)
             assert e.value.status == B.MLP_EINVAL

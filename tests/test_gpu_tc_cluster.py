@@ -91,7 +91,7 @@ def test_minibatch_training_tracks_oracle():
     q, lh, _ = oracle.train(X, y, Params(*W), lr32(), epochs, minibatch=mb)
     assert rel_err_elem(L, lh) <= BF16_GRAD_TOL
     d_gpu, d_ref = got - flat(W), q.flat() - flat(W)
-    assert rel_err_norm(d_gpu, d_ref) <= 2 * BF16_GRAD_TOL
+    assert rel_err_norm(d_gpu, d_ref) <= BF16_GRAD_TOL
     acc_gpu = (oracle.predict(X, unflat(got, H)) == y).mean()
     acc_ref = (oracle.predict(X, q) == y).mean()
     assert abs(acc_gpu - acc_ref) <= 0.01
@@ -146,14 +146,13 @@ def test_nonfinite_loss_is_reported():
 def test_wide_net_65536_row_subset_one_epoch():
     """The wide workload's own schedule on its first 65,536 rows: 48-2048-1,
     mini-batch 8192 (eight updates), against the oracle run of the same
-    schedule: loss within 2e-2, weight change within 4e-2, accuracy within one
-    point."""
+    schedule: loss and weight change within 2e-2, accuracy within one point."""
     n, H, mb = 65536, 2048, 8192
     X, y, W = make(3600, n, H)
     got, L = run(X, y, W, 1, lr32(), mb=mb)
     q, lh, _ = oracle.train(X, y, Params(*W), lr32(), 1, minibatch=mb)
     assert rel_err_elem(L, lh) <= BF16_GRAD_TOL
-    assert rel_err_norm(got - flat(W), q.flat() - flat(W)) <= 2 * BF16_GRAD_TOL
+    assert rel_err_norm(got - flat(W), q.flat() - flat(W)) <= BF16_GRAD_TOL
     acc_gpu = (oracle.predict(X, unflat(got, H)) == y).mean()
     acc_ref = (oracle.predict(X, q) == y).mean()
     assert abs(acc_gpu - acc_ref) <= 0.01
