@@ -571,7 +571,7 @@ C2_WORKLOAD = c2_workload()
 
 
 KERNEL_OF_SHAPE = {0: "k_batched_train", 1: "k_batched_train2", 2: "k_batched_train2", 3: "k_batched_tiled",
-                   4: "k_batched_tiled", 5: "k_batched_tiled"}
+                   4: "k_batched_tiled", 5: "k_batched_tiled", 6: "k_batched_train2"}
 
 
 def c2_shapes(world: int):

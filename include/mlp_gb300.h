@@ -267,7 +267,8 @@ mlp_status mlp_batch_check(mlp_batch_t b, void *stream);
  *      of the weight gradient, all sums in registers), blocks of 4 warps,
  *      rows in chunks of up to 128 (D <= 36);
  *   4  as 3 with chunks of 64 rows (less shared memory, more blocks an SM);
- *   5  as 3 with chunks of 32 rows.
+ *   5  as 3 with chunks of 32 rows;
+ *   6  as 1 at three blocks an SM (registers capped at 168 a thread; D = 33).
  * A new FP32 plan has shape 0.  set: MLP_EINVAL for a shape the plan's D
  * does not take, MLP_EUNSUPPORTED for a BF16 plan.  get: -1 for BF16 plans. */
 mlp_status mlp_batch_set_shape(mlp_batch_t b, int32_t shape);

@@ -105,7 +105,7 @@ def configure(handle, X, y, D, H, n, minibatch=0, act=B.MLP_ACT_SIGMOID):
     return rows
 
 
-BATCH_SHAPES = (0, 1, 2, 3, 4, 5)
+BATCH_SHAPES = (0, 1, 2, 3, 4, 5, 6)
 
 
 def _batch_key(device_name, D, Hs, ns, act):

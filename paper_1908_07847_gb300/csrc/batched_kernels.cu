@@ -149,6 +149,7 @@ bool batched_shape_supported(int D, int shape) {
     if (shape == BATCH_SHAPE_U1) return dp_for(D) != 0;
     if (shape == BATCH_SHAPE_U2_RB1) return batched_u2_supported(D, 1);
     if (shape == BATCH_SHAPE_U2_RB2) return batched_u2_supported(D, 2);
+    if (shape == BATCH_SHAPE_U2_3B) return batched_u2_supported(D, 3);
     if (shape == BATCH_SHAPE_TILED128 || shape == BATCH_SHAPE_TILED64 || shape == BATCH_SHAPE_TILED32)
         return batched_tiled_supported(D, 128);
     return false;
@@ -173,7 +174,7 @@ cudaError_t batched_train(int act, int D, int Hmax, int64_t nmax, const BatchNet
                                    shape == BATCH_SHAPE_TILED32 ? 32 : (shape == BATCH_SHAPE_TILED64 ? 64 : 128), st);
     if (shape != BATCH_SHAPE_U1)
         return batched_train_u2(act, D, Hmax, nets_dev, order_dev, n_nets, epochs, lr, loss_mean, status,
-                                shape == BATCH_SHAPE_U2_RB2 ? 2 : 1, st);
+                                shape == BATCH_SHAPE_U2_RB2 ? 2 : (shape == BATCH_SHAPE_U2_3B ? 3 : 1), st);
     const int DP = dp_for(D);
     if (DP == 0 || Hmax > 128) return cudaErrorInvalidValue;
     if (n_nets == 0 || epochs == 0) return cudaSuccess;

@@ -95,8 +95,8 @@ __device__ __forceinline__ void net_body2(const BatchNet &nd, int D, int epochs,
     __syncthreads();
 }
 
-template <int DQ, int DT, int ACT, int RB>
-__global__ void __launch_bounds__(BNT2, 2) k_batched_train2(const BatchNet *__restrict__ nets,
+template <int DQ, int DT, int ACT, int RB, int MINB = 2>
+__global__ void __launch_bounds__(BNT2, MINB) k_batched_train2(const BatchNet *__restrict__ nets,
                                                            const int *__restrict__ order, int n_nets, int D,
                                                            int epochs, float lr, int loss_mean, int *status,
                                                            int part_floats, int wm_floats) {
@@ -129,10 +129,10 @@ __global__ void __launch_bounds__(BNT2, 2) k_batched_train2(const BatchNet *__re
 }
 
 
-template <int DQ, int DT, int RB>
+template <int DQ, int DT, int RB, int MINB = 2>
 void *pick2(int act) {
-    if (act == MLP_ACT_TANH) return (void *)k_batched_train2<DQ, DT, MLP_ACT_TANH, RB>;
-    return (void *)k_batched_train2<DQ, DT, MLP_ACT_SIGMOID, RB>;
+    if (act == MLP_ACT_TANH) return (void *)k_batched_train2<DQ, DT, MLP_ACT_TANH, RB, MINB>;
+    return (void *)k_batched_train2<DQ, DT, MLP_ACT_SIGMOID, RB, MINB>;
 }
 
 // (DQ, DT) of the input-width class, the row buffer's stride in floats.
@@ -148,7 +148,12 @@ bool width_class(int D, int *DQ, int *DT, int *DPR) {
 
 }  // namespace
 
-bool batched_u2_supported(int D, int rb) { int a, b, c; return width_class(D, &a, &b, &c) && (rb == 1 || D == 33); }
+// rb: rows in flight (1, 2) or 3 = one row in flight at three blocks an SM
+// (168 registers a thread); 2 and 3 only for the paper's D = 33.
+bool batched_u2_supported(int D, int rb) {
+    int a, b, c;
+    return width_class(D, &a, &b, &c) && (rb == 1 || D == 33) && rb >= 1 && rb <= 3;
+}
 
 cudaError_t batched_train_u2(int act, int D, int Hmax, const BatchNet *nets_dev, const int *order_dev, int n_nets,
                              int epochs, float lr, int loss_mean, int *status, int rb, cudaStream_t st) {
@@ -156,7 +161,8 @@ cudaError_t batched_train_u2(int act, int D, int Hmax, const BatchNet *nets_dev,
     if (!batched_u2_supported(D, rb) || Hmax > 128 || !width_class(D, &DQ, &DT, &DPR)) return cudaErrorInvalidValue;
     if (n_nets == 0 || epochs == 0) return cudaSuccess;
     void *fn = nullptr;
-    if (rb == 2) fn = pick2<8, 1, 2>(act);
+    if (rb == 3) fn = pick2<8, 1, 1, 3>(act);
+    else if (rb == 2) fn = pick2<8, 1, 2>(act);
     else if (DT == 1) fn = pick2<8, 1, 1>(act);
     else if (DQ == 2) fn = pick2<2, 0, 1>(act);
     else if (DQ == 4) fn = pick2<4, 0, 1>(act);

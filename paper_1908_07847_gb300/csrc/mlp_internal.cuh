@@ -255,6 +255,7 @@ constexpr int BATCH_SHAPE_U2_RB2 = 2;  // the same with two rows in flight (D = 
 constexpr int BATCH_SHAPE_TILED128 = 3; // register-tiled products, chunks of up to 128 rows
 constexpr int BATCH_SHAPE_TILED64 = 4;  // register-tiled products, chunks of 64 rows (less shared memory)
 constexpr int BATCH_SHAPE_TILED32 = 5;  // register-tiled products, chunks of 32 rows
+constexpr int BATCH_SHAPE_U2_3B = 6;    // two units a lane, three blocks per SM (D = 33 only)
 bool batched_shape_supported(int D, int shape);
 cudaError_t batched_train(int act, int D, int Hmax, int64_t nmax, const BatchNet *nets_dev, const int *order_dev,
                           int n_nets, int epochs, float lr, int loss_mean, int *status, int shape, cudaStream_t st);

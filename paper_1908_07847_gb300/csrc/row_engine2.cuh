@@ -95,11 +95,16 @@ struct RowEngine2 {
                 valid[t] = rr[t] < cn;
                 xo[t] = (valid[t] ? rr[t] : 0) * DPR;
             }
-            float z[RB][U];
+            // Two partial sums a (row, unit), even and odd inputs, so that each
+            // lane has 2 U RB independent multiply-add chains in flight.
+            float z[RB][U], zo[RB][U];
 #pragma unroll
             for (int t = 0; t < RB; ++t)
 #pragma unroll
-                for (int i = 0; i < U; ++i) z[t][i] = b1r[i];
+                for (int i = 0; i < U; ++i) {
+                    z[t][i] = b1r[i];
+                    zo[t][i] = 0.f;
+                }
 #pragma unroll
             for (int q = 0; q < DQ; ++q) {
 #pragma unroll
@@ -108,9 +113,9 @@ struct RowEngine2 {
 #pragma unroll
                     for (int i = 0; i < U; ++i) {
                         z[t][i] = fmaf(xv.x, w[i][4 * q + 0], z[t][i]);
-                        z[t][i] = fmaf(xv.y, w[i][4 * q + 1], z[t][i]);
+                        zo[t][i] = fmaf(xv.y, w[i][4 * q + 1], zo[t][i]);
                         z[t][i] = fmaf(xv.z, w[i][4 * q + 2], z[t][i]);
-                        z[t][i] = fmaf(xv.w, w[i][4 * q + 3], z[t][i]);
+                        zo[t][i] = fmaf(xv.w, w[i][4 * q + 3], zo[t][i]);
                     }
                 }
             }
@@ -125,6 +130,10 @@ struct RowEngine2 {
                         for (int d = 0; d < DT; ++d) z[t][i] = fmaf(xt[d], w[i][4 * DQ + d], z[t][i]);
                 }
             }
+#pragma unroll
+            for (int t = 0; t < RB; ++t)
+#pragma unroll
+                for (int i = 0; i < U; ++i) z[t][i] += zo[t][i];
             // Re-read the rows from shared memory in the backward pass instead of
             // keeping RB x D values live in registers.
             asm volatile("" ::: "memory");

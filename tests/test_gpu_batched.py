@@ -213,7 +213,7 @@ def test_empty_net_and_validation():
     assert e.value.status == B.MLP_EINVAL
 
 
-@pytest.mark.parametrize("shape", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("shape", [1, 2, 3, 4, 5, 6])
 def test_kernel_shapes_match_oracle(shape):
     """The other kernel shapes (two units a lane: segments of 2..32 lanes, one
     and two warps a row; register-tiled: 4 x 4 tiles over row chunks of 128,
@@ -271,7 +271,7 @@ def test_shape_validation_and_autotuner(tmp_path, monkeypatch):
     try:
         assert B.mlp_batch_get_shape(b) == 0
         shape, times = autotune.tune_batched(b, 33, Hs, ns, P, epochs=5, reps=1)
-        assert set(times) == {0, 1, 2, 3, 4, 5} and shape in times and B.mlp_batch_get_shape(b) == shape
+        assert set(times) == {0, 1, 2, 3, 4, 5, 6} and shape in times and B.mlp_batch_get_shape(b) == shape
         assert torch.equal(P, P0)                       # the tuner's launches were undone
         again, _ = autotune.tune_batched(b, 33, Hs, ns, P, epochs=5, reps=1)   # from the cache
         assert again == shape and torch.equal(P, P0)
@@ -291,7 +291,7 @@ def test_shape_validation_and_autotuner(tmp_path, monkeypatch):
     b = B.mlp_batch_create(B.MLP_FP32, 0, 40, [B.mlp_net_desc(10, 40, Xd.data_ptr(), yd.data_ptr(), Pn.data_ptr(),
                                                               None)], lr32(), 1)
     try:
-        for bad in (1, 2, 3, 4, 5, 6, -1):
+        for bad in (1, 2, 3, 4, 5, 6, 7, -1):
             with pytest.raises(B.MLPError) as e:
                 B.mlp_batch_set_shape(b, bad)
             assert e.value.status == B.MLP_EINVAL
