@@ -731,10 +731,11 @@ def run_c2(args, rank, world, local):
     flops = c2_flops(Hs, ns)
     ffma_peak = rates["ffma_tflops"]
     # DRAM bytes of a launch from the committed capture of a reduced case of
-    # the same kernel, scaled by row-epochs (X is read once per epoch or
-    # less), while the kernel's sources still hash to the recorded value
+    # the same kernel, scaled by the rows of the job (rows and weights are
+    # read once a launch and stay on chip for every epoch), while the
+    # kernel's sources still hash to the recorded value
     rec = traffic_record(KERNEL_OF_SHAPE[tuned["shape"]], "c2")
-    traffic = rec["dram_bytes_per_row_epoch"] * float(ns.sum()) * C2_EPOCHS if rec else None
+    traffic = rec["dram_bytes_per_row"] * float(ns.sum()) if rec and "dram_bytes_per_row" in rec else None
     sigmoids = float(np.sum(ns * (Hs + 1))) * C2_EPOCHS
     out = {
         "metric": METRIC, "value": value, "unit": "sample-steps/s", "n_gpus": world,

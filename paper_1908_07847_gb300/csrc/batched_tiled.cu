@@ -2,7 +2,9 @@
 // small register-tiled products (inputs up to 36 wide).  The method per net is
 // the one of batched_kernels.cu (Sec. 2.2 of arXiv 1908.07847: feed-forward,
 // output error, backpropagation, full-batch gradient descent without
-// momentum); only the schedule differs.  Per chunk of up to `ncap` rows:
+// momentum); only the schedule differs.  Per pass of rows (as many as the
+// h / d1 buffer holds at the net's own width; X^T holds up to 128 rows, a
+// net's whole set when it fits):
 //
 //   1. Z = [X | 1] [W1 | b1]^T, every thread a 4-row x 4-unit tile of Z with
 //      its 16 sums in registers (one 16-byte word of X^T and one of W^T a
@@ -17,10 +19,10 @@
 // At the end of the epoch each thread applies its own tiles' update to the
 // transposed weights in shared memory; gw2, gb2, the loss and the gradient
 // norm are summed in fixed orders.  Every sum has one fixed order, so a run
-// is bitwise reproducible.  X^T (ncap columns), W^T, and h / d1 (ncap rows)
+// is bitwise reproducible.  X^T (ncap columns), W^T, and h / d1 (hcap rows)
 // live in shared memory; padding rows of X^T and padding units of W^T and w2
 // are zero, so their d1 and their share of z2 are zero and they add nothing.
-// Nets with more than ncap rows stream their rows in chunks.
+// Nets with more than 128 rows stream their rows in chunks of 128.
 #include "mlp_internal.cuh"
 
 namespace mlp {
@@ -33,26 +35,28 @@ constexpr int TSLOTS = 3;         // gradient tiles a thread holds (<= 32 x 10 t
 struct TLayout {
     int K;       // D + 1 (the ones column carries the bias)
     int KQ;      // K rounded up to 4, / 4
-    int ncap;    // rows per chunk (multiple of 4)
+    int ncap;    // rows of X^T held at a time (multiple of 4; all of a net's rows when they fit)
+    int hcap;    // rows of h / d1 a pass computes (multiple of 4, <= ncap)
     int HP;      // Hmax rounded up to 4
-    int HSS;     // row stride of h / d1 (HP + 4: rows fall in different banks)
+    int HSS;     // h / d1 buffer: hcap rows of HP + 4 floats (nets narrower than Hmax fit more rows)
     // float offsets
     int xt, wt, hs, w2, d2, gwp, red;
     int total;
 };
 
-__host__ __device__ inline TLayout t_layout(int D, int Hmax, int ncap) {
+__host__ __device__ inline TLayout t_layout(int D, int Hmax, int ncap, int hcap) {
     TLayout L;
     L.K = D + 1;
     L.KQ = (L.K + 3) / 4;
     L.ncap = ncap;
+    L.hcap = hcap;
     L.HP = (Hmax + 3) & ~3;
     L.HSS = L.HP + 4;
     L.xt = 0;                                   // X^T: 4 KQ rows x ncap
     L.wt = L.xt + 4 * L.KQ * ncap;              // W^T: 4 KQ rows x HP
-    L.hs = L.wt + 4 * L.KQ * L.HP;              // h / d1: ncap x HSS
-    L.w2 = L.hs + ncap * L.HSS;                 // w2: HP
-    L.d2 = L.w2 + L.HP;                         // d2: ncap
+    L.hs = L.wt + 4 * L.KQ * L.HP;              // h / d1: hcap x HSS
+    L.w2 = L.hs + hcap * L.HSS;                 // w2: HP
+    L.d2 = L.w2 + L.HP;                         // d2: ncap (a pass never exceeds it)
     L.gwp = L.d2 + ncap;                        // gw2 partials: TNT x 4
     L.red = L.gwp + 4 * TNT;                    // reductions: 4 warps x (sse, gb2) + 4 doubles
     L.total = L.red + 32;
@@ -103,6 +107,11 @@ __device__ __forceinline__ void net_tiled(const BatchNet &nd, int D, int epochs,
     const int T2 = HQ * KQ;             // gradient tiles (4 units x 4 inputs)
     const int RS = TNT / HQ;            // row subsets of step 3
     const int uq3 = tid % HQ, rs3 = tid / HQ;
+    // h / d1 rows are as wide as this net's units (in 16-byte words: HQ,
+    // plus one or two so that the stride is odd and rows start in different
+    // banks); a pass takes as many rows as the buffer holds at that stride
+    const int hss = 4 * (HQ + 1 + (HQ & 1));
+    const int hpass = min(128, ((L.hcap * L.HSS) / hss) & ~3);
 
     for (int e = 0; e < epochs; ++e) {
         float g[TSLOTS][4][4];
@@ -116,105 +125,112 @@ __device__ __forceinline__ void net_tiled(const BatchNet &nd, int D, int epochs,
         float sse_f = 0.f, gb2_f = 0.f;
 
         for (int64_t r0 = 0; r0 < n; r0 += L.ncap) {
-            const int nc = (int)min((int64_t)L.ncap, n - r0);
-            const int nc4 = (nc + 3) & ~3;
+            const int ncx = (int)min((int64_t)L.ncap, n - r0);
             if (!resident) {
                 __syncthreads();
-                load_chunk(r0, nc);
+                load_chunk(r0, ncx);
                 __syncthreads();
             }
-            // ---- 1. Z = [X | 1] [W1 | b1]^T by 4 x 4 tiles, h = f(Z)
-            const int T1 = (nc4 / 4) * HQ;
-            for (int t = tid; t < T1; t += TNT) {
-                const int rq = t / HQ, uq = t - rq * HQ;
-                float z[4][4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) z[i][u] = 0.f;
-                const float *xa = XT + 4 * rq, *wb = WT + 4 * uq;
-#pragma unroll 2
-                for (int k = 0; k < K; ++k) {
-                    const float4 a = *reinterpret_cast<const float4 *>(xa + k * L.ncap);
-                    const float4 b = *reinterpret_cast<const float4 *>(wb + k * HP);
-                    const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+            // passes of up to hcap rows over the rows of X^T held
+            for (int h0 = 0; h0 < ncx; h0 += hpass) {
+                const int nc = min(hpass, ncx - h0);
+                const int nc4 = (nc + 3) & ~3;
+                const float *XTc = XT + h0;   // column h0 of X^T: this pass's first row
+                if (h0 > 0) __syncthreads();  // the previous pass is done with h / d1
+                // ---- 1. Z = [X | 1] [W1 | b1]^T by 4 x 4 tiles, h = f(Z)
+                const int T1 = (nc4 / 4) * HQ;
+                for (int t = tid; t < T1; t += TNT) {
+                    const int rq = t / HQ, uq = t - rq * HQ;
+                    float z[4][4];
 #pragma unroll
                     for (int i = 0; i < 4; ++i)
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) z[i][u] = fmaf(av[i], bv[u], z[i][u]);
-                }
+                        for (int u = 0; u < 4; ++u) z[i][u] = 0.f;
+                    const float *xa = XTc + 4 * rq, *wb = WT + 4 * uq;
+#pragma unroll 2
+                    for (int k = 0; k < K; ++k) {
+                        const float4 a = *reinterpret_cast<const float4 *>(xa + k * L.ncap);
+                        const float4 b = *reinterpret_cast<const float4 *>(wb + k * HP);
+                        const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
-                for (int i = 0; i < 4; ++i)
-                    *reinterpret_cast<float4 *>(HS + (4 * rq + i) * L.HSS + 4 * uq) =
-                        make_float4(Act<ACT>::f(z[i][0]), Act<ACT>::f(z[i][1]), Act<ACT>::f(z[i][2]),
-                                    Act<ACT>::f(z[i][3]));
-            }
-            __syncthreads();
-            // ---- 2. one thread a row: z2, o, d2 (rows nc .. nc4 - 1 get d2 = 0)
-            for (int r = tid; r < nc4; r += TNT) {
-                float d2 = 0.f;
-                if (r < nc) {
-                    const float *hr = HS + r * L.HSS;
-                    float za = 0.f, zb = 0.f;
-                    for (int q = 0; q < HQ; ++q) {
-                        const float4 h4 = *reinterpret_cast<const float4 *>(hr + 4 * q);
-                        const float4 w4 = *reinterpret_cast<const float4 *>(w2s + 4 * q);
-                        za = fmaf(h4.x, w4.x, za);
-                        zb = fmaf(h4.y, w4.y, zb);
-                        za = fmaf(h4.z, w4.z, za);
-                        zb = fmaf(h4.w, w4.w, zb);
+                        for (int i = 0; i < 4; ++i)
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) z[i][u] = fmaf(av[i], bv[u], z[i][u]);
                     }
-                    const float o = sigmoid_out((za + zb) + b2);
-                    const float err = o - nd.y[r0 + r];
-                    d2 = c * err * o * (1.0f - o);
-                    sse_f = fmaf(err, err, sse_f);
-                    gb2_f += d2;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        *reinterpret_cast<float4 *>(HS + (4 * rq + i) * hss + 4 * uq) =
+                            make_float4(Act<ACT>::f(z[i][0]), Act<ACT>::f(z[i][1]), Act<ACT>::f(z[i][2]),
+                                        Act<ACT>::f(z[i][3]));
                 }
-                d2s[r] = d2;
-            }
-            __syncthreads();
-            // ---- 3. d1 = d2 w2 f'(h) over h; partial gw2 = sum h d2 per row subset
-            if (rs3 < RS) {
-                const float4 w4 = *reinterpret_cast<const float4 *>(w2s + 4 * uq3);
-                for (int r = rs3; r < nc4; r += RS) {
-                    float *hp = HS + r * L.HSS + 4 * uq3;
-                    const float4 h4 = *reinterpret_cast<const float4 *>(hp);
-                    const float d2 = d2s[r];
-                    gw2a[0] = fmaf(h4.x, d2, gw2a[0]);
-                    gw2a[1] = fmaf(h4.y, d2, gw2a[1]);
-                    gw2a[2] = fmaf(h4.z, d2, gw2a[2]);
-                    gw2a[3] = fmaf(h4.w, d2, gw2a[3]);
-                    *reinterpret_cast<float4 *>(hp) =
-                        make_float4(d2 * w4.x * dact<ACT>(h4.x), d2 * w4.y * dact<ACT>(h4.y),
-                                    d2 * w4.z * dact<ACT>(h4.z), d2 * w4.w * dact<ACT>(h4.w));
+                __syncthreads();
+                // ---- 2. one thread a row: z2, o, d2 (rows nc .. nc4 - 1 get d2 = 0)
+                for (int r = tid; r < nc4; r += TNT) {
+                    float d2 = 0.f;
+                    if (r < nc) {
+                        const float *hr = HS + r * hss;
+                        float za = 0.f, zb = 0.f, zc = 0.f, zd = 0.f;
+                        for (int q = 0; q < HQ; ++q) {
+                            const float4 h4 = *reinterpret_cast<const float4 *>(hr + 4 * q);
+                            const float4 w4 = *reinterpret_cast<const float4 *>(w2s + 4 * q);
+                            za = fmaf(h4.x, w4.x, za);
+                            zb = fmaf(h4.y, w4.y, zb);
+                            zc = fmaf(h4.z, w4.z, zc);
+                            zd = fmaf(h4.w, w4.w, zd);
+                        }
+                        const float o = sigmoid_out(((za + zb) + (zc + zd)) + b2);
+                        const float err = o - nd.y[r0 + h0 + r];
+                        d2 = c * err * o * (1.0f - o);
+                        sse_f = fmaf(err, err, sse_f);
+                        gb2_f += d2;
+                    }
+                    d2s[r] = d2;
                 }
-            }
-            __syncthreads();
-            // ---- 4. [gW1 | gb1] += d1^T [X | 1], 4 rows at a time
+                __syncthreads();
+                // ---- 3. d1 = d2 w2 f'(h) over h; partial gw2 = sum h d2 per row subset
+                if (rs3 < RS) {
+                    const float4 w4 = *reinterpret_cast<const float4 *>(w2s + 4 * uq3);
+                    for (int r = rs3; r < nc4; r += RS) {
+                        float *hp = HS + r * hss + 4 * uq3;
+                        const float4 h4 = *reinterpret_cast<const float4 *>(hp);
+                        const float d2 = d2s[r];
+                        gw2a[0] = fmaf(h4.x, d2, gw2a[0]);
+                        gw2a[1] = fmaf(h4.y, d2, gw2a[1]);
+                        gw2a[2] = fmaf(h4.z, d2, gw2a[2]);
+                        gw2a[3] = fmaf(h4.w, d2, gw2a[3]);
+                        *reinterpret_cast<float4 *>(hp) =
+                            make_float4(d2 * w4.x * dact<ACT>(h4.x), d2 * w4.y * dact<ACT>(h4.y),
+                                        d2 * w4.z * dact<ACT>(h4.z), d2 * w4.w * dact<ACT>(h4.w));
+                    }
+                }
+                __syncthreads();
+                // ---- 4. [gW1 | gb1] += d1^T [X | 1], 4 rows at a time
 #pragma unroll
-            for (int s = 0; s < TSLOTS; ++s) {
-                const int t = tid + s * TNT;
-                if (t < T2) {
-                    const int kq = t / HQ, uq = t - kq * HQ;
-                    const float *da = HS + 4 * uq;
-                    const float *xb = XT + 4 * kq * L.ncap;
-                    for (int rr = 0; rr < nc4; rr += 4) {
-                        float4 dv[4], xv[4];
+                for (int s = 0; s < TSLOTS; ++s) {
+                    const int t = tid + s * TNT;
+                    if (t < T2) {
+                        const int kq = t / HQ, uq = t - kq * HQ;
+                        const float *da = HS + 4 * uq;
+                        const float *xb = XTc + 4 * kq * L.ncap;
+                        for (int rr = 0; rr < nc4; rr += 4) {
+                            float4 dv[4], xv[4];
 #pragma unroll
-                        for (int i = 0; i < 4; ++i) dv[i] = *reinterpret_cast<const float4 *>(da + (rr + i) * L.HSS);
+                            for (int i = 0; i < 4; ++i)
+                                dv[i] = *reinterpret_cast<const float4 *>(da + (rr + i) * hss);
 #pragma unroll
-                        for (int k = 0; k < 4; ++k) xv[k] = *reinterpret_cast<const float4 *>(xb + k * L.ncap + rr);
+                            for (int k = 0; k < 4; ++k) xv[k] = *reinterpret_cast<const float4 *>(xb + k * L.ncap + rr);
 #pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            const float d[4] = {dv[i].x, dv[i].y, dv[i].z, dv[i].w};
-                            const float xr[4] = {i == 0 ? xv[0].x : i == 1 ? xv[0].y : i == 2 ? xv[0].z : xv[0].w,
-                                                 i == 0 ? xv[1].x : i == 1 ? xv[1].y : i == 2 ? xv[1].z : xv[1].w,
-                                                 i == 0 ? xv[2].x : i == 1 ? xv[2].y : i == 2 ? xv[2].z : xv[2].w,
-                                                 i == 0 ? xv[3].x : i == 1 ? xv[3].y : i == 2 ? xv[3].z : xv[3].w};
+                            for (int i = 0; i < 4; ++i) {
+                                const float d[4] = {dv[i].x, dv[i].y, dv[i].z, dv[i].w};
+                                const float xr[4] = {i == 0 ? xv[0].x : i == 1 ? xv[0].y : i == 2 ? xv[0].z : xv[0].w,
+                                                     i == 0 ? xv[1].x : i == 1 ? xv[1].y : i == 2 ? xv[1].z : xv[1].w,
+                                                     i == 0 ? xv[2].x : i == 1 ? xv[2].y : i == 2 ? xv[2].z : xv[2].w,
+                                                     i == 0 ? xv[3].x : i == 1 ? xv[3].y : i == 2 ? xv[3].z : xv[3].w};
 #pragma unroll
-                            for (int u = 0; u < 4; ++u)
+                                for (int u = 0; u < 4; ++u)
 #pragma unroll
-                                for (int k = 0; k < 4; ++k) g[s][u][k] = fmaf(d[u], xr[k], g[s][u][k]);
+                                    for (int k = 0; k < 4; ++k) g[s][u][k] = fmaf(d[u], xr[k], g[s][u][k]);
+                            }
                         }
                     }
                 }
@@ -249,7 +265,10 @@ __device__ __forceinline__ void net_tiled(const BatchNet &nd, int D, int epochs,
             if (want_gn) gn = fma((double)v, (double)v, gn);
         }
         b2 -= lr * gb2;
-        // this thread's tiles of [gW1 | gb1] update W^T (row D of W^T is b1)
+        // this thread's tiles of [gW1 | gb1] update W^T (row D of W^T is b1),
+        // a 16-byte word a row of the tile.  Padding units (j >= H) and inputs
+        // (k > D) have zero gradient (their d1, or their X^T row, is zero), so
+        // the whole word is updated and their weights stay zero.
 #pragma unroll
         for (int s = 0; s < TSLOTS; ++s) {
             const int t = tid + s * TNT;
@@ -257,16 +276,16 @@ __device__ __forceinline__ void net_tiled(const BatchNet &nd, int D, int epochs,
                 const int kq = t / HQ, uq = t - kq * HQ;
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    const int kk = 4 * kq + k;
-                    if (kk < K) {
+                    float4 *wp = reinterpret_cast<float4 *>(WT + (4 * kq + k) * HP + 4 * uq);
+                    float4 w = *wp;
+                    w.x -= lr * g[s][0][k];
+                    w.y -= lr * g[s][1][k];
+                    w.z -= lr * g[s][2][k];
+                    w.w -= lr * g[s][3][k];
+                    *wp = w;
+                    if (want_gn) {
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            const int j = 4 * uq + u;
-                            if (j < H) {
-                                WT[kk * HP + j] -= lr * g[s][u][k];
-                                if (want_gn) gn = fma((double)g[s][u][k], (double)g[s][u][k], gn);
-                            }
-                        }
+                        for (int u = 0; u < 4; ++u) gn = fma((double)g[s][u][k], (double)g[s][u][k], gn);
                     }
                 }
             }
@@ -303,10 +322,10 @@ __device__ __forceinline__ void net_tiled(const BatchNet &nd, int D, int epochs,
 
 template <int ACT>
 __global__ void __launch_bounds__(TNT) k_batched_tiled(const BatchNet *__restrict__ nets, const int *__restrict__ order,
-                                                       int n_nets, int D, int Hmax, int ncap, int epochs, float lr,
-                                                       int loss_mean, int *status) {
+                                                       int n_nets, int D, int Hmax, int ncap, int hcap, int epochs,
+                                                       float lr, int loss_mean, int *status) {
     extern __shared__ __align__(16) float smem[];
-    const TLayout L = t_layout(D, Hmax, ncap);
+    const TLayout L = t_layout(D, Hmax, ncap, hcap);
     // every region is written before it is read (padding rows and units of
     // h hold finite values whose d1, and whose weight in z2, are 0)
     for (int i = threadIdx.x; i < L.total; i += TNT) smem[i] = 0.f;
@@ -329,22 +348,27 @@ __global__ void __launch_bounds__(TNT) k_batched_tiled(const BatchNet *__restric
 
 bool batched_tiled_supported(int D, int Hmax) { return D >= 1 && D <= 36 && Hmax >= 1 && Hmax <= 128; }
 
-size_t batched_tiled_smem(int D, int Hmax, int ncap) { return sizeof(float) * (size_t)t_layout(D, Hmax, ncap).total; }
+size_t batched_tiled_smem(int D, int Hmax, int ncap, int hcap) {
+    return sizeof(float) * (size_t)t_layout(D, Hmax, ncap, hcap).total;
+}
 
 cudaError_t batched_train_tiled(int act, int D, int Hmax, int64_t nmax, const BatchNet *nets_dev,
                                 const int *order_dev, int n_nets, int epochs, float lr, int loss_mean, int *status,
-                                int ncap_max, cudaStream_t st) {
+                                int hcap_max, cudaStream_t st) {
     if (!batched_tiled_supported(D, Hmax)) return cudaErrorInvalidValue;
     if (n_nets == 0 || epochs == 0) return cudaSuccess;
+    // X^T holds a net's rows up to 128 (resident across epochs); h / d1 holds
+    // hcap_max rows, a pass
     int ncap = (int)((nmax + 3) & ~(int64_t)3);
-    if (ncap > ncap_max) ncap = ncap_max;
+    if (ncap > 128) ncap = 128;
     if (ncap < 4) ncap = 4;
-    const size_t smem = batched_tiled_smem(D, Hmax, ncap);
+    const int hcap = ncap < hcap_max ? ncap : hcap_max;
+    const size_t smem = batched_tiled_smem(D, Hmax, ncap, hcap);
     void *fn = act == MLP_ACT_TANH ? (void *)k_batched_tiled<MLP_ACT_TANH> : (void *)k_batched_tiled<MLP_ACT_SIGMOID>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     void *args[] = {(void *)&nets_dev, (void *)&order_dev, (void *)&n_nets, (void *)&D, (void *)&Hmax,
-                    (void *)&ncap, (void *)&epochs, (void *)&lr, (void *)&loss_mean, (void *)&status};
+                    (void *)&ncap, (void *)&hcap, (void *)&epochs, (void *)&lr, (void *)&loss_mean, (void *)&status};
     return cudaLaunchKernel(fn, dim3((unsigned)n_nets), dim3(TNT), args, smem, st);
 }
 

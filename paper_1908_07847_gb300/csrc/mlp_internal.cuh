@@ -252,18 +252,18 @@ void batched_smem_layout(int D, int Hmax, int *part_floats, int *wm_floats, size
 constexpr int BATCH_SHAPE_U1 = 0;      // one hidden unit a lane, blocks of 8 warps, two per SM
 constexpr int BATCH_SHAPE_U2_RB1 = 1;  // two units a lane, blocks of 4 warps, two per SM, one row in flight
 constexpr int BATCH_SHAPE_U2_RB2 = 2;  // the same with two rows in flight (D = 33 only)
-constexpr int BATCH_SHAPE_TILED128 = 3; // register-tiled products, chunks of up to 128 rows
-constexpr int BATCH_SHAPE_TILED64 = 4;  // register-tiled products, chunks of 64 rows (less shared memory)
-constexpr int BATCH_SHAPE_TILED32 = 5;  // register-tiled products, chunks of 32 rows
+constexpr int BATCH_SHAPE_TILED128 = 3; // register-tiled products, passes of up to 128 rows
+constexpr int BATCH_SHAPE_TILED64 = 4;  // register-tiled products, passes of 64 rows (less shared memory)
+constexpr int BATCH_SHAPE_TILED32 = 5;  // register-tiled products, passes of 32 rows
 constexpr int BATCH_SHAPE_U2_3B = 6;    // two units a lane, three blocks per SM (D = 33 only)
 bool batched_shape_supported(int D, int shape);
 cudaError_t batched_train(int act, int D, int Hmax, int64_t nmax, const BatchNet *nets_dev, const int *order_dev,
                           int n_nets, int epochs, float lr, int loss_mean, int *status, int shape, cudaStream_t st);
 bool batched_tiled_supported(int D, int Hmax);
-size_t batched_tiled_smem(int D, int Hmax, int ncap);
+size_t batched_tiled_smem(int D, int Hmax, int ncap, int hcap);
 cudaError_t batched_train_tiled(int act, int D, int Hmax, int64_t nmax, const BatchNet *nets_dev,
                                 const int *order_dev, int n_nets, int epochs, float lr, int loss_mean, int *status,
-                                int ncap_max, cudaStream_t st);
+                                int hcap_max, cudaStream_t st);
 cudaError_t batched_train_u2(int act, int D, int Hmax, const BatchNet *nets_dev, const int *order_dev, int n_nets,
                              int epochs, float lr, int loss_mean, int *status, int rb, cudaStream_t st);
 bool batched_u2_supported(int D, int rb);
