@@ -147,7 +147,7 @@ __device__ __forceinline__ void net_tiled(const BatchNet &nd, int D, int epochs,
 #pragma unroll
                         for (int u = 0; u < 4; ++u) z[i][u] = 0.f;
                     const float *xa = XTc + 4 * rq, *wb = WT + 4 * uq;
-#pragma unroll 2
+#pragma unroll 4
                     for (int k = 0; k < K; ++k) {
                         const float4 a = *reinterpret_cast<const float4 *>(xa + k * L.ncap);
                         const float4 b = *reinterpret_cast<const float4 *>(wb + k * HP);
