@@ -147,7 +147,7 @@ __device__ __forceinline__ void net_tiled(const BatchNet &nd, int D, int epochs,
 #pragma unroll
                         for (int u = 0; u < 4; ++u) z[i][u] = 0.f;
                     const float *xa = XTc + 4 * rq, *wb = WT + 4 * uq;
-#pragma unroll 4
+#pragma unroll 8
                     for (int k = 0; k < K; ++k) {
                         const float4 a = *reinterpret_cast<const float4 *>(xa + k * L.ncap);
                         const float4 b = *reinterpret_cast<const float4 *>(wb + k * HP);
@@ -239,10 +239,8 @@ __device__ __forceinline__ void net_tiled(const BatchNet &nd, int D, int epochs,
         }
 
         // ---- end of epoch: reductions in fixed orders, then the update
-        if (rs3 < RS) {
-#pragma unroll
-            for (int u = 0; u < 4; ++u) gwp[rs3 * 4 * HQ + 4 * uq3 + u] = gw2a[u];
-        }
+        if (rs3 < RS)
+            *reinterpret_cast<float4 *>(gwp + rs3 * 4 * HQ + 4 * uq3) = make_float4(gw2a[0], gw2a[1], gw2a[2], gw2a[3]);
         sse_f = warp_sum(sse_f);
         gb2_f = warp_sum(gb2_f);
         if (lane == 0) {
