@@ -595,9 +595,9 @@ def c2_net(t: int, n: int, H: int):
             I.init_weights(I.subseed(C2_SEED, 200 + t), D_IN, int(H)))
 
 
-def c2_flops(Hs, ns, epochs=C2_EPOCHS):
-    """Algorithmic FLOPs: 4 D H + 10 H per row-epoch (forward 2 D H + 3 H,
-    backward 2 D H + 7 H)."""
+def c2_flops(Hs, ns, epochs):
+    """Algorithmic FLOPs of `epochs` epochs: 4 D H + 10 H per row-epoch
+    (forward 2 D H + 3 H, backward 2 D H + 7 H)."""
     return float(np.sum(ns * (4 * D_IN * Hs + 10 * Hs))) * epochs
 
 
@@ -728,7 +728,7 @@ def run_c2(args, rank, world, local):
     units = int(ns_all.sum()) * C2_EPOCHS
     value = units * args.steps / T_f
     launch_s = statistics.mean(kt)
-    flops = c2_flops(Hs, ns)
+    flops = c2_flops(Hs, ns, C2_EPOCHS)
     ffma_peak = rates["ffma_tflops"]
     # DRAM bytes of a launch from the committed capture of a reduced case of
     # the same kernel, scaled by the rows of the job (rows and weights are
@@ -759,7 +759,7 @@ def run_c2(args, rank, world, local):
                 "h2d_bytes_per_step": int(Xh.numel() * 4 + yh.numel() * 4 + Pin.numel() * 4),
                 "d2h_bytes_per_step": int(Pout.numel() * 4 + Lh.numel() * 8),
                 "call": "mlp_batch_run_host (pinned host rows, labels and initial weights in; trained weights "
-                        "and 500-epoch loss histories out; one launch)",
+                        "and %d-epoch loss histories out; one launch)" % C2_EPOCHS,
                 "same_weights_as_device_path": e2e_same},
         "plain_fp32": {"value": plain, "unit": "sample-steps/s",
                        "path": "mlp_step_plain on one mid-size net of the workload (the plain path takes one net "
@@ -804,7 +804,7 @@ def c2_oracle_leg(sample, P_gpu, offs_p):
            "sample": "%d of the nets (%d rows), all %d epochs (FP64 C oracle, OpenMP over nets)"
                      % (len(onets), rows, C2_EPOCHS), **host_cpu()}
     parity = {"nets": len(onets), "epochs": C2_EPOCHS,
-              "measure": "max over nets of max |w - w*| / max |w*| after the benchmark's 500 epochs",
+              "measure": "max over nets of max |w - w*| / max |w*| after the benchmark's %d epochs" % C2_EPOCHS,
               "value": err, "tolerance": 1e-4}
     return cpu, parity
 
