@@ -23,6 +23,15 @@
 // live in shared memory; padding rows of X^T and padding units of W^T and w2
 // are zero, so their d1 and their share of z2 are zero and they add nothing.
 // Nets with more than 128 rows stream their rows in chunks of 128.
+//
+// The products are bound by shared-memory bandwidth, so tiles are handed to
+// lanes for the fewest wavefronts.  A 16-byte load is served a half-warp at a
+// time; the two quarter-warps of a half share one wavefront only if the
+// distinct words they read add up to at most 128 bytes, without two of them in
+// one bank.  Both products therefore give a quarter-warp 4 unit quads x 2 row
+// (or input) quads, so a load reads at most 4 distinct words a quarter, and
+// X^T rows are 4 mod 8 words apart so that neighbouring input quads sit in
+// different banks.
 #include "mlp_internal.cuh"
 
 namespace mlp {
@@ -36,6 +45,8 @@ struct TLayout {
     int K;       // D + 1 (the ones column carries the bias)
     int KQ;      // K rounded up to 4, / 4
     int ncap;    // rows of X^T held at a time (multiple of 4; all of a net's rows when they fit)
+    int xs;      // row stride of X^T: ncap, or ncap + 4, whichever is 4 mod 8 (so that the rows of
+                 //   two neighbouring input quads start 16 words apart: no bank conflict between them)
     int hcap;    // rows of h / d1 a pass computes (multiple of 4, <= ncap)
     int HP;      // Hmax rounded up to 4
     int HSS;     // h / d1 buffer: hcap rows of HP + 4 floats (nets narrower than Hmax fit more rows)
@@ -49,11 +60,12 @@ __host__ __device__ inline TLayout t_layout(int D, int Hmax, int ncap, int hcap)
     L.K = D + 1;
     L.KQ = (L.K + 3) / 4;
     L.ncap = ncap;
+    L.xs = (ncap & 7) ? ncap : ncap + 4;
     L.hcap = hcap;
     L.HP = (Hmax + 3) & ~3;
     L.HSS = L.HP + 4;
-    L.xt = 0;                                   // X^T: 4 KQ rows x ncap
-    L.wt = L.xt + 4 * L.KQ * ncap;              // W^T: 4 KQ rows x HP
+    L.xt = 0;                                   // X^T: 4 KQ rows x xs
+    L.wt = L.xt + 4 * L.KQ * L.xs;              // W^T: 4 KQ rows x HP
     L.hs = L.wt + 4 * L.KQ * L.HP;              // h / d1: hcap x HSS
     L.w2 = L.hs + hcap * L.HSS;                 // w2: HP
     L.d2 = L.w2 + L.HP;                         // d2: ncap (a pass never exceeds it)
@@ -63,8 +75,49 @@ __host__ __device__ inline TLayout t_layout(int D, int Hmax, int ncap, int hcap)
     return L;
 }
 
-template <int ACT>
-__device__ __forceinline__ float dact(float h) { return Act<ACT>::df(h); }
+// Hidden-unit activation.  Sigmoid (Eq. 1) as 1 / (1 + 2^(-x log2 e)): one
+// exp2 and one reciprocal (ex2.approx, rcp.approx refined by a Newton step),
+// half the instructions of the output unit's sigmoid_f32.  It drops that
+// function's split-constant reduction, so its error is bounded in absolute
+// terms: the relative error of 2^(-x log2 e) grows like |x| 2^-24 while the
+// value it feeds, sigmoid(x), shrinks like e^x for x < 0.  Measured on the
+// GPU against FP64 over [-100, 100]: absolute error <= 9.2e-8; relative
+// error <= 2.6e-7 for x >= -3 and <= 5.0e-7 for x >= -8.
+// Inputs below -87 are raised to -87 so that 1 + e stays finite (the result
+// is then below 2e-38); NaN passes through.
+template <int ACT> __device__ __forceinline__ float hidden_f(float x) { return Act<ACT>::f(x); }
+template <> __device__ __forceinline__ float hidden_f<MLP_ACT_SIGMOID>(float x) {
+    const float L2E = 1.44269504088896341f;
+    x = x < -87.0f ? -87.0f : x;
+    float e;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(-x * L2E));
+    const float d = 1.0f + e;
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(d));
+    return fmaf(r, fmaf(-d, r, 1.0f), r);
+}
+
+// f'(z) through the value h = f(z), as one fused multiply-add: h - h^2 for
+// sigmoid, 1 - h^2 for tanh.
+template <int ACT> __device__ __forceinline__ float dact(float h);
+template <> __device__ __forceinline__ float dact<MLP_ACT_SIGMOID>(float h) { return fmaf(-h, h, h); }
+template <> __device__ __forceinline__ float dact<MLP_ACT_TANH>(float h) { return fmaf(-h, h, 1.0f); }
+
+// Gradient tile t (of HQ x KQ) -> its input quad kq and unit quad uq.  Input
+// quads go in pairs, unit-major inside a pair, so a quarter-warp covers 4 unit
+// quads x 2 input quads (at most 4 distinct 16-byte words a load: one
+// wavefront a half-warp); an odd last input quad follows, unit-major.
+__device__ __forceinline__ void grad_tile(int t, int HQ, int KQ, int &kq, int &uq) {
+    const int TA = (KQ >> 1) * 2 * HQ;
+    if (t < TA) {
+        const int p = t / (2 * HQ), rem = t - p * 2 * HQ;
+        uq = rem >> 1;
+        kq = 2 * p + (rem & 1);
+    } else {
+        uq = t - TA;
+        kq = KQ - 1;
+    }
+}
 
 template <int ACT>
 __device__ __forceinline__ void net_tiled(const BatchNet &nd, int D, int epochs, float lr, int loss_mean,
@@ -94,7 +147,7 @@ __device__ __forceinline__ void net_tiled(const BatchNet &nd, int D, int epochs,
             const int k = i / cols, r = i - k * cols;
             float v = 0.f;
             if (r < nc) v = k < D ? nd.X[(r0 + r) * D + k] : (k == D ? 1.f : 0.f);
-            XT[i] = v;
+            XT[k * L.xs + r] = v;
         }
     };
     const bool resident = n <= L.ncap;
@@ -138,9 +191,16 @@ __device__ __forceinline__ void net_tiled(const BatchNet &nd, int D, int epochs,
                 const float *XTc = XT + h0;   // column h0 of X^T: this pass's first row
                 if (h0 > 0) __syncthreads();  // the previous pass is done with h / d1
                 // ---- 1. Z = [X | 1] [W1 | b1]^T by 4 x 4 tiles, h = f(Z)
-                const int T1 = (nc4 / 4) * HQ;
+                // tiles in pairs of row quads, unit-major inside a pair: a
+                // quarter-warp covers 2 row quads x 4 unit quads, so each of its
+                // 16-byte loads touches at most 4 distinct words (one wavefront
+                // a half-warp); an odd last row quad leaves its pair's second
+                // half idle
+                const int RQ = nc4 >> 2, T1 = ((RQ + 1) >> 1) * 2 * HQ;
                 for (int t = tid; t < T1; t += TNT) {
-                    const int rq = t / HQ, uq = t - rq * HQ;
+                    const int rp = t / (2 * HQ), rem = t - rp * 2 * HQ;
+                    const int uq = rem >> 1, rq = 2 * rp + (rem & 1);
+                    if (rq >= RQ) continue;
                     float z[4][4];
 #pragma unroll
                     for (int i = 0; i < 4; ++i)
@@ -149,7 +209,7 @@ __device__ __forceinline__ void net_tiled(const BatchNet &nd, int D, int epochs,
                     const float *xa = XTc + 4 * rq, *wb = WT + 4 * uq;
 #pragma unroll 8
                     for (int k = 0; k < K; ++k) {
-                        const float4 a = *reinterpret_cast<const float4 *>(xa + k * L.ncap);
+                        const float4 a = *reinterpret_cast<const float4 *>(xa + k * L.xs);
                         const float4 b = *reinterpret_cast<const float4 *>(wb + k * HP);
                         const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
@@ -160,8 +220,8 @@ __device__ __forceinline__ void net_tiled(const BatchNet &nd, int D, int epochs,
 #pragma unroll
                     for (int i = 0; i < 4; ++i)
                         *reinterpret_cast<float4 *>(HS + (4 * rq + i) * hss + 4 * uq) =
-                            make_float4(Act<ACT>::f(z[i][0]), Act<ACT>::f(z[i][1]), Act<ACT>::f(z[i][2]),
-                                        Act<ACT>::f(z[i][3]));
+                            make_float4(hidden_f<ACT>(z[i][0]), hidden_f<ACT>(z[i][1]), hidden_f<ACT>(z[i][2]),
+                                        hidden_f<ACT>(z[i][3]));
                 }
                 __syncthreads();
                 // ---- 2. one thread a row: z2, o, d2 (rows nc .. nc4 - 1 get d2 = 0)
@@ -199,8 +259,8 @@ __device__ __forceinline__ void net_tiled(const BatchNet &nd, int D, int epochs,
                         gw2a[2] = fmaf(h4.z, d2, gw2a[2]);
                         gw2a[3] = fmaf(h4.w, d2, gw2a[3]);
                         *reinterpret_cast<float4 *>(hp) =
-                            make_float4(d2 * w4.x * dact<ACT>(h4.x), d2 * w4.y * dact<ACT>(h4.y),
-                                        d2 * w4.z * dact<ACT>(h4.z), d2 * w4.w * dact<ACT>(h4.w));
+                            make_float4((d2 * w4.x) * dact<ACT>(h4.x), (d2 * w4.y) * dact<ACT>(h4.y),
+                                        (d2 * w4.z) * dact<ACT>(h4.z), (d2 * w4.w) * dact<ACT>(h4.w));
                     }
                 }
                 __syncthreads();
@@ -209,16 +269,17 @@ __device__ __forceinline__ void net_tiled(const BatchNet &nd, int D, int epochs,
                 for (int s = 0; s < TSLOTS; ++s) {
                     const int t = tid + s * TNT;
                     if (t < T2) {
-                        const int kq = t / HQ, uq = t - kq * HQ;
+                        int kq, uq;
+                        grad_tile(t, HQ, KQ, kq, uq);
                         const float *da = HS + 4 * uq;
-                        const float *xb = XTc + 4 * kq * L.ncap;
+                        const float *xb = XTc + 4 * kq * L.xs;
                         for (int rr = 0; rr < nc4; rr += 4) {
                             float4 dv[4], xv[4];
 #pragma unroll
                             for (int i = 0; i < 4; ++i)
                                 dv[i] = *reinterpret_cast<const float4 *>(da + (rr + i) * hss);
 #pragma unroll
-                            for (int k = 0; k < 4; ++k) xv[k] = *reinterpret_cast<const float4 *>(xb + k * L.ncap + rr);
+                            for (int k = 0; k < 4; ++k) xv[k] = *reinterpret_cast<const float4 *>(xb + k * L.xs + rr);
 #pragma unroll
                             for (int i = 0; i < 4; ++i) {
                                 const float d[4] = {dv[i].x, dv[i].y, dv[i].z, dv[i].w};
@@ -271,7 +332,8 @@ __device__ __forceinline__ void net_tiled(const BatchNet &nd, int D, int epochs,
         for (int s = 0; s < TSLOTS; ++s) {
             const int t = tid + s * TNT;
             if (t < T2) {
-                const int kq = t / HQ, uq = t - kq * HQ;
+                int kq, uq;
+                grad_tile(t, HQ, KQ, kq, uq);
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     float4 *wp = reinterpret_cast<float4 *>(WT + (4 * kq + k) * HP + 4 * uq);
