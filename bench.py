@@ -1062,6 +1062,35 @@ def run_c4(args, rank, world, local):
             times.append(e0.elapsed_time(e1) * 1e-3)
     assert B.mlp_batch_check(plan, stream) == B.MLP_OK, B.mlp_last_error()
     B.mlp_batch_destroy(plan)
+    dev_w = Pw.cpu().numpy()
+    # e2e: the same training through the host-buffer entry point (bf16 rows,
+    # labels and initial weights in; trained weights and loss histories out)
+    Xh = Xall.cpu().pin_memory()
+    yh = yall.cpu().pin_memory()
+    Pin = P0.cpu().pin_memory()
+    Pout = torch.empty_like(Pin).pin_memory()
+    Lh = torch.empty((n_nets, epochs), dtype=torch.float64).pin_memory()
+    hplan = B.mlp_batch_create_host(B.MLP_BF16, B.MLP_ACT_SIGMOID, C4_D, [C4_H] * n_nets, ns, epochs, LR, 1)
+    B.mlp_batch_run_host(hplan, Xh, yh, Pin, Pout, Lh, epochs, stream)
+    t_e2e = []
+    for _ in range(max(2, args.steps // 2)):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        B.mlp_batch_run_host(hplan, Xh, yh, Pin, Pout, Lh, epochs, stream)
+        e1.record()
+        torch.cuda.synchronize()
+        t_e2e.append(e0.elapsed_time(e1) * 1e-3)
+    B.mlp_batch_destroy(hplan)
+    e2e_same = bool(np.array_equal(Pout.numpy(), dev_w))
+    T_e = aggregate_max(sum(t_e2e), world)
+    e2e = {"value": int(ns.sum()) * epochs * world * len(t_e2e) / T_e, "unit": "sample-steps/s",
+           "h2d_bytes_per_step": int(Xh.numel() * 2 + yh.numel() * 4 + Pin.numel() * 4),
+           "d2h_bytes_per_step": int(Pout.numel() * 4 + Lh.numel() * 8),
+           "call": "mlp_batch_run_host (pinned host bf16 rows, labels and initial weights in; trained weights "
+                   "and %d-epoch loss histories out; one launch)" % epochs,
+           "same_weights_as_device_path": e2e_same}
+    del Xh
     # the plain path on net 0 (separate kernels per step, FP32 arithmetic on its
     # bf16 rows), for the speedup of the one-launch tensor-core kernel over it
     hp = B.mlp_create(C4_D, C4_H, LR, 1, B.MLP_BF16, B.MLP_ACT_SIGMOID)
@@ -1093,7 +1122,7 @@ def run_c4(args, rank, world, local):
         "plain_fp32": {"value": plain, "unit": "sample-steps/s",
                        "path": "mlp_step_plain on one net of the workload (FP32 arithmetic on bf16 rows)",
                        "speedup_of_tensor_core": units * args.steps / T_f / plain},
-        "gpu_launches": args.steps, "clocks": clk.summary(),
+        "e2e": e2e, "gpu_launches": args.steps, "clocks": clk.summary(),
     }
     if rank == 0:
         out["cpu_baseline"], out["parity"] = c4_oracle_leg(seed, ns)
