@@ -59,7 +59,9 @@ def parse():
                     help="c2 / c4: nets per GPU (default 4096 / 1024; fewer for profiling captures)")
     ap.add_argument("--epochs", type=int, default=0, help="c2 / c4: epochs per step (default 500 / 200)")
     ap.add_argument("--shape", type=int, default=-1,
-                    help="c2 only: FP32 many-nets kernel shape (0, 1, 2); default: the autotuner's pick")
+                    help="c2 only: FP32 many-nets kernel shape (0..6); default: the autotuner's pick")
+    ap.add_argument("--clusters", type=int, default=0,
+                    help="c3 only: thread-block clusters of the wide-net kernel; default: the autotuner's pick")
     ap.add_argument("--workload", default="c2", choices=["c0", "c1", "c2", "c3", "c4"],
                     help="c0: the 33-16-1 net on the 120-row cohort, 1000 epochs per step; "
                          "c1: the 33-64-1 full-batch workload on 4096 rows, one epoch per step; "
@@ -925,6 +927,15 @@ def run_c3(args, rank, world, local):
     rates = unit_rates()
     h = B.mlp_create(C3_D, C3_H, LR, 1, B.MLP_BF16, B.MLP_ACT_SIGMOID)
     B.mlp_set_weights(h, *W)
+    # cluster count: the autotuner's pick for this shape (untimed), unless given
+    from paper_1908_07847_gb300 import autotune
+    if args.clusters > 0:
+        tuned = {"clusters": args.clusters, "source": "--clusters"}
+    else:
+        k, us = autotune.tune_clusters(X, y, C3_D, C3_H, C3_N, C3_MB)
+        tuned = {"clusters": k, "source": "autotune.tune_clusters", "us_per_step": us,
+                 "limit": B.mlp_cluster_limit(C3_H)}
+    B.mlp_set_clusters(h, tuned["clusters"])
     loss = torch.zeros(1, dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
@@ -987,7 +998,7 @@ def run_c3(args, rank, world, local):
                      "frac": mma_flops / launch_s / 1e12 / peak, "traffic": None, "kernel": "k_tc_cluster",
                      "peak_basis": "bf16_tflops_sustained of measured", "flops_per_launch": mma_flops,
                      "sfu": sfu_roofline(float(C3_N) * (C3_H + 1), launch_s, rates)},
-        "gpu_launches": args.steps, "clocks": clk.summary(),
+        "gpu_launches": args.steps, "clocks": clk.summary(), "kernel_shape": tuned,
     }
     if rank == 0:
         out["cpu_baseline"], out["parity"] = c3_oracle_leg(X, W)

@@ -207,6 +207,21 @@ mlp_status mlp_debug_skip_block(mlp_t net, int32_t skip_block);
  * the same fixed-point rounding of the gradient as a multi-block launch. */
 mlp_status mlp_set_rows_per_block(mlp_t net, int32_t rows);
 
+/* Thread-block clusters of the bf16 wide-network kernel (MLP_PATH_TC_CLUSTER;
+ * tuning knob, no counterpart in the paper).  Each mini-batch's 128-row tiles
+ * are dealt round-robin to K clusters of H/256 blocks, and at the end of every
+ * step the K clusters' gradient slices are summed in cluster order: more
+ * clusters give each fewer tiles but add partial slices to the sum.
+ * mlp_set_clusters caps K at `clusters` (>= 1; 0 restores the default, the
+ * most clusters the device keeps resident at once, which is also the upper
+ * limit; K never exceeds the tiles of a step).  Results for different K agree
+ * within the bf16 bars but not bit for bit (the sum order follows K).
+ * mlp_cluster_limit writes that device limit for hidden width H (a multiple of
+ * 256, at most 2048) on the current device to *clusters (1 if the occupancy
+ * query fails). */
+mlp_status mlp_set_clusters(mlp_t net, int32_t clusters);
+mlp_status mlp_cluster_limit(int32_t H, int32_t *clusters);
+
 /*
  * Many independent networks trained in one launch (the paper trains its male
  * and female subsets as separate networks, Sec. 2.1; here any number, each with

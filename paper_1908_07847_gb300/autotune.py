@@ -9,6 +9,10 @@
   register-tiled products over row chunks of 128, 64 or 32 rows (which trade
   shared memory for blocks an SM).  Which is fastest depends on the plan's mix
   of widths and row counts.
+* ``tune_clusters``: the cluster count of the bf16 wide-network kernel
+  (mlp_set_clusters): a step's 128-row tiles are dealt to the clusters, whose
+  gradient slices are then summed; fewer clusters mean more tiles each but a
+  shorter cross-cluster sum.
 
 Each times its candidates on the caller's device and workload and caches the
 fastest in a JSON file (``$MLP_GB300_TUNE_CACHE``, else
@@ -169,3 +173,66 @@ def tune_batched(plan, D, Hs, ns, params, act=B.MLP_ACT_SIGMOID, epochs=25, reps
         if use_cache:
             _store(table)
     return best, times
+
+
+def _cluster_key(device_name, D, H, mb, act):
+    return "%s|clusters|D=%d|H=%d|mb=%d|act=%d" % (device_name, D, H, mb, act)
+
+
+def tune_clusters(X, y, D, H, n, minibatch, act=B.MLP_ACT_SIGMOID, candidates=None, steps=8, reps=3,
+                  use_cache=True):
+    """Best cluster count for the bf16 wide-network kernel (mlp_set_clusters)
+    on mini-batches of `minibatch` rows of width D and H hidden units.
+
+    X (bf16 rows, n >= minibatch) and y: device tensors; their values do not
+    matter for timing (a throw-away handle with lr 0 trains `steps`
+    mini-batches a launch).  Candidates default to the device limit and the
+    six counts below it, plus half the limit.  Returns (clusters, {candidate:
+    microseconds per mini-batch step})."""
+    import torch
+    dev_name = torch.cuda.get_device_name()
+    key = _cluster_key(dev_name, D, H, minibatch, act)
+    with _lock:
+        table = _load() if use_cache else {}
+        if key in table:
+            return int(table[key]["clusters"]), {int(k): v for k, v in table[key]["us_per_step"].items()}
+    kmax = B.mlp_cluster_limit(H)
+    if candidates is None:
+        candidates = sorted({k for k in range(max(1, kmax - 6), kmax + 1)} | {max(1, kmax // 2)})
+    rows = min(int(n), int(steps) * int(minibatch))
+    nsteps = (rows + minibatch - 1) // minibatch
+    stream = torch.cuda.current_stream().cuda_stream
+    h = B.mlp_create(D, H, 0.0, 1, B.MLP_BF16, act)   # lr 0: timing only
+    times = {}
+    try:
+        if B.mlp_train_path(h, rows, minibatch) != B.MLP_PATH_TC_CLUSTER:
+            raise ValueError("tune_clusters: this shape does not run on the wide-network kernel")
+        for k in candidates:
+            B.mlp_set_clusters(h, int(k))
+            B.mlp_train_epochs(h, X, y, rows, 1, minibatch, None, None, stream)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                B.mlp_train_epochs(h, X, y, rows, 1, minibatch, None, None, stream)
+            e1.record()
+            torch.cuda.synchronize()
+            times[int(k)] = e0.elapsed_time(e1) * 1e3 / (reps * nsteps)
+        if B.mlp_check(h, stream) != B.MLP_OK:
+            raise B.MLPError(B.MLP_ECUDA, "autotune run failed: " + B.mlp_last_error())
+    finally:
+        B.mlp_destroy(h)
+    best = min(times, key=times.get)
+    with _lock:
+        table = _load() if use_cache else {}
+        table[key] = {"clusters": best, "us_per_step": {str(k): v for k, v in times.items()}}
+        if use_cache:
+            _store(table)
+    return best, times
+
+
+def configure_clusters(handle, X, y, D, H, n, minibatch, act=B.MLP_ACT_SIGMOID):
+    """Tune (or read the cache) and set the handle's cluster count."""
+    k, _ = tune_clusters(X, y, D, H, n, minibatch, act)
+    B.mlp_set_clusters(handle, k)
+    return k

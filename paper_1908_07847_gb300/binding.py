@@ -25,7 +25,8 @@ EXPORTS = [
     "mlp_create", "mlp_destroy", "mlp_set_weights", "mlp_get_weights", "mlp_weights_device",
     "mlp_forward", "mlp_backward", "mlp_update", "mlp_step_plain", "mlp_train_epochs",
     "mlp_train_host", "mlp_train_path", "mlp_predict", "mlp_check", "mlp_workspace_bytes", "mlp_forward_w",
-    "mlp_backward_w", "mlp_debug_skip_block", "mlp_set_rows_per_block", "mlp_batch_train",
+    "mlp_backward_w", "mlp_debug_skip_block", "mlp_set_rows_per_block", "mlp_set_clusters",
+    "mlp_cluster_limit", "mlp_batch_train",
     "mlp_batch_create", "mlp_batch_run", "mlp_batch_check", "mlp_batch_destroy", "mlp_batch_create_host",
     "mlp_batch_run_host", "mlp_batch_set_shape", "mlp_batch_get_shape", "mlp_train_fused_noalloc",
     "mlp_zscore_workspace_bytes", "mlp_zscore", "mlp_unit_rates", "mlp_last_error", "mlp_version",
@@ -88,6 +89,8 @@ def lib():
             "mlp_backward_w": (S, [I32, I32, I32, I32, I64, V, V, V, V, V, V, V, V, V, V, V, V, U64, V]),
             "mlp_debug_skip_block": (S, [V, I32]),
             "mlp_set_rows_per_block": (S, [V, I32]),
+            "mlp_set_clusters": (S, [V, I32]),
+            "mlp_cluster_limit": (S, [I32, ctypes.POINTER(I32)]),
             "mlp_batch_train": (S, [I32, I32, I32, ctypes.POINTER(mlp_net_desc), I32, I32, F, I32, V]),
             "mlp_batch_create": (S, [I32, I32, I32, ctypes.POINTER(mlp_net_desc), I32, F, I32, ctypes.POINTER(V)]),
             "mlp_batch_run": (S, [V, I32, V]),
@@ -212,6 +215,18 @@ def mlp_debug_skip_block(h, b):
 
 def mlp_set_rows_per_block(h, rows):
     return _ck(lib().mlp_set_rows_per_block(h, rows))
+
+
+def mlp_set_clusters(h, clusters):
+    """Cap the bf16 wide-network kernel's cluster count (0 = the default)."""
+    return _ck(lib().mlp_set_clusters(h, clusters))
+
+
+def mlp_cluster_limit(H):
+    """Most clusters of H/256 blocks the current device keeps resident."""
+    k = ctypes.c_int32()
+    _ck(lib().mlp_cluster_limit(H, ctypes.byref(k)))
+    return k.value
 
 
 # ------------------------------------------------------------ handle-free API

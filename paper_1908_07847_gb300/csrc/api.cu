@@ -503,6 +503,20 @@ mlp_status mlp_set_rows_per_block(mlp_t h, int32_t rows) {
     return MLP_OK;
 }
 
+mlp_status mlp_set_clusters(mlp_t h, int32_t clusters) {
+    if (check_handle(h)) return MLP_EINVAL;
+    if (clusters < 0) return fail(MLP_EINVAL, "mlp_set_clusters: clusters must be >= 0");
+    h->max_clusters = clusters == 0 ? (1 << 30) : clusters;
+    return MLP_OK;
+}
+
+mlp_status mlp_cluster_limit(int32_t H, int32_t *clusters) {
+    if (!clusters || H < 256 || H > 2048 || H % 256 != 0)
+        return fail(MLP_EINVAL, "mlp_cluster_limit: H must be a multiple of 256 in 256..2048");
+    *clusters = mlp::tc_cluster_max_clusters(H);
+    return MLP_OK;
+}
+
 mlp_status mlp_workspace_bytes(int32_t prec, int32_t D, int32_t H, int64_t n, uint64_t *bytes) {
     if (!bytes || D < 1 || H < 1 || n < 0 || prec < MLP_FP32 || prec > MLP_FP64)
         return fail(MLP_EINVAL, "mlp_workspace_bytes: bad arguments");

@@ -246,3 +246,40 @@ def test_wide_net_20_epochs_against_stored_oracle_run():
     w0 = WL.kept_params(*W, WL.C3_KEEP_EVERY)
     w = WL.kept_params(pg.W1, pg.b1, pg.w2, pg.b2, WL.C3_KEEP_EVERY)
     assert rel_err_norm(w - w0, np.asarray(gold["kept_params"]) - w0) <= BF16_GRAD_TOL
+
+
+def test_cluster_count_knob_and_tuner(tmp_path, monkeypatch):
+    """The cluster count (mlp_set_clusters) changes how a step's tiles are
+    dealt and the order of the cross-cluster sum, not the method: 1, 3 and
+    the default cluster counts each train within the bf16 bar of the oracle.
+    The tuner picks one of its candidates, caches it, and bad values are
+    refused."""
+    import torch
+    from paper_1908_07847_gb300 import autotune
+    monkeypatch.setenv("MLP_GB300_TUNE_CACHE", str(tmp_path / "tune.json"))
+    H, n, mb, epochs, lr = 1024, 6000, 2048, 2, 0.5
+    kmax = B.mlp_cluster_limit(H)
+    assert kmax >= 1
+    with pytest.raises(B.MLPError) as e:
+        B.mlp_cluster_limit(300)
+    assert e.value.status == B.MLP_EINVAL
+    X, y, W = make(3900, n, H)
+    q, _, _ = oracle.train(X, y, Params(*W), float(np.float32(lr)), epochs, minibatch=mb)
+    dref = q.flat() - flat(W)
+    Xd = dev(I.bf16_bits(X).view(np.int16))
+    yd = dev(y)
+    for k in (1, 3, 0):
+        with Net(D_PAD, H, lr, 1, B.MLP_BF16, B.MLP_ACT_SIGMOID) as net:
+            net.set(W)
+            with pytest.raises(B.MLPError):
+                B.mlp_set_clusters(net.h, -1)
+            B.mlp_set_clusters(net.h, k)
+            B.mlp_train_epochs(net.h, Xd, yd, n, epochs, mb, None, None, stream())
+            assert net.check() == B.MLP_OK, B.mlp_last_error()
+            assert rel_err_norm(net.flat() - flat(W), dref) <= BF16_GRAD_TOL, k
+    cands = sorted({1, max(1, kmax - 1), kmax})
+    best, times = autotune.tune_clusters(Xd, yd, D_PAD, H, n, mb, candidates=cands, steps=2, reps=1)
+    assert best in cands and set(times) == set(cands)
+    again, _ = autotune.tune_clusters(Xd, yd, D_PAD, H, n, mb, candidates=cands, steps=2, reps=1)
+    assert again == best
+    torch.cuda.synchronize()
