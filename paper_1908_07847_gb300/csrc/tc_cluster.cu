@@ -645,11 +645,19 @@ size_t tc_cluster_scratch_bytes(int D, int H) {
 }
 
 int tc_cluster_max_clusters(int H) {
+    // cached per device and cluster size (devices may differ in SM count)
+    constexpr int MAXDEV = 64;
     static std::mutex mu;
-    static int cache[9] = {0};
+    static int cache[MAXDEV][9] = {};
     const int S = H / HS;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAXDEV) {
+        cudaGetLastError();
+        dev = 0;
+    }
     std::lock_guard<std::mutex> lk(mu);
-    if (cache[S] == 0) {
+    int &slot = cache[dev][S];
+    if (slot == 0) {
         cudaFuncSetAttribute(k_tc_cluster<MLP_ACT_SIGMOID>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM_ALLOC);
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)S);
@@ -668,9 +676,9 @@ int tc_cluster_max_clusters(int H) {
             cudaGetLastError();
             n = 1;
         }
-        cache[S] = n;
+        slot = n;
     }
-    return cache[S];
+    return slot;
 }
 
 cudaError_t tc_cluster_train(const void *X, const float *y, float *params, int D, int H, int64_t n, int epochs,
