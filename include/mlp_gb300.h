@@ -114,6 +114,25 @@ mlp_status mlp_backward(mlp_t net, const void *X, const void *y, int64_t n,
 mlp_status mlp_update(mlp_t net, const void *gW1, const void *gb1,
                       const void *gw2, const void *gb2, void *stream);
 
+/* Exchange step of data-parallel training of one network across ranks.  The
+ * gradient of a mini-batch (Sec. 2.2) is a sum over its rows, so ranks that
+ * each hold a shard of the rows compute summed (loss_mean = 0) gradients and
+ * every rank then adds all ranks' vectors in rank order:
+ *   out[i] = scale * (((parts[0][i] + parts[1][i]) + parts[2][i]) + ...)
+ * with parts an nparts x len row-major device array of floats (rank p's flat
+ * gradient [gW1, gb1, gw2, gb2] at parts + p * len) and out a device array of
+ * len floats (not overlapping parts); scale is 1/m for the mean loss over a
+ * mini-batch of m rows, else 1.  If loss_parts (nparts device doubles: each
+ * rank's summed shard loss) is given, *loss_acc (one device double) is
+ * increased by loss_scale times their rank-order sum; loss_parts and loss_acc
+ * are both given or both NULL.  Asynchronous on `stream`; the same inputs give
+ * the same bits on every rank.  MLP_EINVAL for nparts < 1, len < 0 or missing
+ * pointers. */
+mlp_status mlp_grad_sum(const float *parts, const double *loss_parts,
+                        int32_t nparts, int64_t len, float scale,
+                        double loss_scale, float *out, double *loss_acc,
+                        void *stream);
+
 /* One training step by the plain path: separate forward, output, gradient,
  * reduction and update kernels with the hidden activations materialised in
  * device memory.  Same result as one full-batch epoch of mlp_train_epochs. */

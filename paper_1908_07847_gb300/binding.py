@@ -23,7 +23,7 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "lib
 # Every symbol the header declares (checked by the CPU tests).
 EXPORTS = [
     "mlp_create", "mlp_destroy", "mlp_set_weights", "mlp_get_weights", "mlp_weights_device",
-    "mlp_forward", "mlp_backward", "mlp_update", "mlp_step_plain", "mlp_train_epochs",
+    "mlp_forward", "mlp_backward", "mlp_update", "mlp_grad_sum", "mlp_step_plain", "mlp_train_epochs",
     "mlp_train_host", "mlp_train_path", "mlp_predict", "mlp_check", "mlp_workspace_bytes", "mlp_forward_w",
     "mlp_backward_w", "mlp_debug_skip_block", "mlp_set_rows_per_block", "mlp_set_clusters",
     "mlp_cluster_limit", "mlp_batch_train",
@@ -90,6 +90,7 @@ def lib():
             "mlp_debug_skip_block": (S, [V, I32]),
             "mlp_set_rows_per_block": (S, [V, I32]),
             "mlp_set_clusters": (S, [V, I32]),
+            "mlp_grad_sum": (S, [V, V, I32, I64, F, ctypes.c_double, V, V, V]),
             "mlp_cluster_limit": (S, [I32, ctypes.POINTER(I32)]),
             "mlp_batch_train": (S, [I32, I32, I32, ctypes.POINTER(mlp_net_desc), I32, I32, F, I32, V]),
             "mlp_batch_create": (S, [I32, I32, I32, ctypes.POINTER(mlp_net_desc), I32, F, I32, ctypes.POINTER(V)]),
@@ -215,6 +216,13 @@ def mlp_debug_skip_block(h, b):
 
 def mlp_set_rows_per_block(h, rows):
     return _ck(lib().mlp_set_rows_per_block(h, rows))
+
+
+def mlp_grad_sum(parts, loss_parts, nparts, length, scale, loss_scale, out, loss_acc, stream=0):
+    """out = scale * rank-order sum of the nparts x length gradient rows in
+    parts; loss_acc += loss_scale * rank-order sum of loss_parts."""
+    return _ck(lib().mlp_grad_sum(_p(parts), _p(loss_parts), nparts, length, scale, loss_scale, _p(out),
+                                  _p(loss_acc), stream))
 
 
 def mlp_set_clusters(h, clusters):
