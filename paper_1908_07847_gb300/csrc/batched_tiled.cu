@@ -3,8 +3,9 @@
 // the one of batched_kernels.cu (Sec. 2.2 of arXiv 1908.07847: feed-forward,
 // output error, backpropagation, full-batch gradient descent without
 // momentum); only the schedule differs.  Per pass of rows (as many as the
-// h / d1 buffer holds at the net's own width; X^T holds up to 128 rows, a
-// net's whole set when it fits):
+// h / d1 buffer holds at the net's own width -- W^T is stored at the net's
+// own width too and the buffer takes the rest of the space the widest net of
+// the launch needs; X^T holds up to 128 rows, a net's whole set when it fits):
 //
 //   1. Z = [X | 1] [W1 | b1]^T, every thread a 4-row x 4-unit tile of Z with
 //      its 16 sums in registers (one 16-byte word of X^T and one of W^T a
@@ -124,16 +125,20 @@ __device__ __forceinline__ void net_tiled(const BatchNet &nd, int D, int epochs,
                                           int *status, float *sm, const TLayout &L) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int H = nd.H, K = L.K, HQ = (H + 3) / 4, HP = L.HP;
+    // W^T rows are as wide as this net's units (HN floats); the h / d1 buffer
+    // starts right after them, so a net narrower than the widest of the
+    // launch gets the rest of the widest net's W^T as extra h / d1 rows
+    const int HN = 4 * HQ;
     const int64_t n = nd.n;
-    float *XT = sm + L.xt, *WT = sm + L.wt, *HS = sm + L.hs, *w2s = sm + L.w2, *d2s = sm + L.d2;
+    float *XT = sm + L.xt, *WT = sm + L.wt, *HS = sm + L.wt + 4 * L.KQ * HN, *w2s = sm + L.w2, *d2s = sm + L.d2;
     float *gwp = sm + L.gwp, *red = sm + L.red;
     double *redd = (double *)(red + 16);
     const float *P = nd.params;
     const int HD = H * D;
 
     // W^T (row k < D: W1[., k]; row D: b1; rows above and units >= H: 0), w2
-    for (int i = tid; i < 4 * L.KQ * HP; i += TNT) {
-        const int k = i / HP, j = i - k * HP;
+    for (int i = tid; i < 4 * L.KQ * HN; i += TNT) {
+        const int k = i / HN, j = i - k * HN;
         float v = 0.f;
         if (j < H) v = k < D ? P[j * D + k] : (k == D ? P[HD + j] : 0.f);
         WT[i] = v;
@@ -164,7 +169,7 @@ __device__ __forceinline__ void net_tiled(const BatchNet &nd, int D, int epochs,
     // plus one or two so that the stride is odd and rows start in different
     // banks); a pass takes as many rows as the buffer holds at that stride
     const int hss = 4 * (HQ + 1 + (HQ & 1));
-    const int hpass = min(128, ((L.hcap * L.HSS) / hss) & ~3);
+    const int hpass = min(128, ((L.w2 - (L.wt + 4 * L.KQ * HN)) / hss) & ~3);
 
     for (int e = 0; e < epochs; ++e) {
         float g[TSLOTS][4][4];
@@ -210,7 +215,7 @@ __device__ __forceinline__ void net_tiled(const BatchNet &nd, int D, int epochs,
 #pragma unroll 8
                     for (int k = 0; k < K; ++k) {
                         const float4 a = *reinterpret_cast<const float4 *>(xa + k * L.xs);
-                        const float4 b = *reinterpret_cast<const float4 *>(wb + k * HP);
+                        const float4 b = *reinterpret_cast<const float4 *>(wb + k * HN);
                         const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
                         for (int i = 0; i < 4; ++i)
@@ -336,7 +341,7 @@ __device__ __forceinline__ void net_tiled(const BatchNet &nd, int D, int epochs,
                 grad_tile(t, HQ, KQ, kq, uq);
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    float4 *wp = reinterpret_cast<float4 *>(WT + (4 * kq + k) * HP + 4 * uq);
+                    float4 *wp = reinterpret_cast<float4 *>(WT + (4 * kq + k) * HN + 4 * uq);
                     float4 w = *wp;
                     w.x -= lr * g[s][0][k];
                     w.y -= lr * g[s][1][k];
@@ -370,10 +375,10 @@ __device__ __forceinline__ void net_tiled(const BatchNet &nd, int D, int epochs,
     float *Pw = nd.params;
     for (int i = tid; i < HD; i += TNT) {
         const int j = i / D, k = i - j * D;
-        Pw[i] = WT[k * HP + j];
+        Pw[i] = WT[k * HN + j];
     }
     for (int j = tid; j < H; j += TNT) {
-        Pw[HD + j] = WT[D * HP + j];
+        Pw[HD + j] = WT[D * HN + j];
         Pw[HD + H + j] = w2s[j];
     }
     if (tid == 0) Pw[HD + 2 * H] = b2;
