@@ -706,14 +706,15 @@ def run_c2(args, rank, world, local):
     e2e_steps = max(3, args.steps // 4)
     B.mlp_batch_run_host(hplan, Xh, yh, Pin, Pout, Lh, C2_EPOCHS, stream)
     t_e2e = []
-    for _ in range(e2e_steps):
-        flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        B.mlp_batch_run_host(hplan, Xh, yh, Pin, Pout, Lh, C2_EPOCHS, stream)
-        e1.record()
-        torch.cuda.synchronize()
-        t_e2e.append(e0.elapsed_time(e1) * 1e-3)
+    with ClockSampler(local) as clk_e2e:
+        for _ in range(e2e_steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            B.mlp_batch_run_host(hplan, Xh, yh, Pin, Pout, Lh, C2_EPOCHS, stream)
+            e1.record()
+            torch.cuda.synchronize()
+            t_e2e.append(e0.elapsed_time(e1) * 1e-3)
     B.mlp_batch_destroy(hplan)
     e2e_same = bool(np.array_equal(Pout.numpy(), Pw.cpu().numpy()))
 
@@ -762,7 +763,7 @@ def run_c2(args, rank, world, local):
                 "d2h_bytes_per_step": int(Pout.numel() * 4 + Lh.numel() * 8),
                 "call": "mlp_batch_run_host (pinned host rows, labels and initial weights in; trained weights "
                         "and %d-epoch loss histories out; one launch)" % C2_EPOCHS,
-                "same_weights_as_device_path": e2e_same},
+                "same_weights_as_device_path": e2e_same, "clocks": clk_e2e.summary()},
         "plain_fp32": {"value": plain, "unit": "sample-steps/s",
                        "path": "mlp_step_plain on one mid-size net of the workload (the plain path takes one net "
                                "at a time)", "speedup_of_batched": value / world / plain},
@@ -1084,14 +1085,15 @@ def run_c4(args, rank, world, local):
     hplan = B.mlp_batch_create_host(B.MLP_BF16, B.MLP_ACT_SIGMOID, C4_D, [C4_H] * n_nets, ns, epochs, LR, 1)
     B.mlp_batch_run_host(hplan, Xh, yh, Pin, Pout, Lh, epochs, stream)
     t_e2e = []
-    for _ in range(max(2, args.steps // 2)):
-        flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        B.mlp_batch_run_host(hplan, Xh, yh, Pin, Pout, Lh, epochs, stream)
-        e1.record()
-        torch.cuda.synchronize()
-        t_e2e.append(e0.elapsed_time(e1) * 1e-3)
+    with ClockSampler(local) as clk_e2e:
+        for _ in range(max(2, args.steps // 2)):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            B.mlp_batch_run_host(hplan, Xh, yh, Pin, Pout, Lh, epochs, stream)
+            e1.record()
+            torch.cuda.synchronize()
+            t_e2e.append(e0.elapsed_time(e1) * 1e-3)
     B.mlp_batch_destroy(hplan)
     e2e_same = bool(np.array_equal(Pout.numpy(), dev_w))
     T_e = aggregate_max(sum(t_e2e), world)
@@ -1100,7 +1102,7 @@ def run_c4(args, rank, world, local):
            "d2h_bytes_per_step": int(Pout.numel() * 4 + Lh.numel() * 8),
            "call": "mlp_batch_run_host (pinned host bf16 rows, labels and initial weights in; trained weights "
                    "and %d-epoch loss histories out; one launch)" % epochs,
-           "same_weights_as_device_path": e2e_same}
+           "same_weights_as_device_path": e2e_same, "clocks": clk_e2e.summary()}
     del Xh
     # the plain path on net 0 (separate kernels per step, FP32 arithmetic on its
     # bf16 rows), for the speedup of the one-launch tensor-core kernel over it
