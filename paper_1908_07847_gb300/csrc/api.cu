@@ -641,7 +641,7 @@ static mlp_status batch_create_tc(int32_t act, int32_t D, const mlp_net_desc *ne
     char *base = (char *)b->mem;
     b->tc_descs = base + maps;
     b->order = (int *)(base + maps + descs);
-    b->status = (int *)(base + maps + descs + ords);
+    b->status = (int *)(base + maps + descs + ords);   // status, and 64 bytes on the net counter
     std::vector<unsigned char> hmaps(mb * N1, 0), hdescs(db * N1, 0);
     for (int t = 0; t < n_nets; ++t) {
         const mlp_net_desc &d = nets[t];
@@ -750,7 +750,7 @@ mlp_status mlp_batch_run(mlp_batch_t b, int32_t epochs, void *stream) {
         if ((int64_t)epochs * b->max_tiles > (int64_t)INT32_MAX)
             return fail(MLP_EINVAL, "mlp_batch_run: epochs x tiles of the largest net beyond 2^31; split the epochs");
         CK(mlp::tc_batched_train(b->tc_descs, b->order, b->n_nets, b->D, epochs, b->lr, b->loss_mean, b->act,
-                                 b->status, (cudaStream_t)stream),
+                                 b->status, b->status + 16, (cudaStream_t)stream),
            "tensor-core batched training kernel");
         return MLP_OK;
     }

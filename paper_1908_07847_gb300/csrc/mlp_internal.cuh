@@ -277,7 +277,7 @@ cudaError_t tc_encode_map(void *map, const void *X, int D, int64_t n);
 void tc_fill_desc(void *desc, const void *tmap_dev, const float *y, float *params, double *loss_hist,
                   double *gnorm_hist, int64_t n, int H);
 cudaError_t tc_batched_train(const void *descs_dev, const int *order_dev, int n_nets, int D, int epochs, float lr,
-                             int loss_mean, int act, int *status, cudaStream_t st);
+                             int loss_mean, int act, int *status, int *next, cudaStream_t st);
 
 // One wide network (H = 256..2048, a multiple of 256) trained by clusters of
 // H/256 blocks; scratch of tc_cluster_scratch_bytes(), all zero before the first

@@ -90,6 +90,7 @@ struct TcArgs {
     int loss_mean;
     int act;                  // hidden activation (mlp_activation)
     int *status;
+    int *next;                // nets taken after the first wave (zeroed before the launch), or NULL
 };
 
 using namespace tcd;
@@ -149,7 +150,19 @@ __global__ void __launch_bounds__(NT, 1) k_tc_batched(TcArgs a) {
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    for (int idx = blockIdx.x; idx < a.n_nets; idx += gridDim.x) {
+    // Nets go to blocks in decreasing cost: block b takes net b first, then
+    // each block that finishes takes the next net not yet taken (one atomic
+    // increment), so the longest nets start first and no block waits on a
+    // fixed share; which block trains a net does not change its result.
+    int *s_idx = (int *)(sm + SM_MISC + 32);
+    auto next_net = [&](int cur) -> int {
+        if (!a.next) return cur + (int)gridDim.x;
+        __syncthreads();
+        if (tid == 0) *s_idx = (int)gridDim.x + atomicAdd(a.next, 1);
+        __syncthreads();
+        return *s_idx;
+    };
+    for (int idx = blockIdx.x; idx < a.n_nets; idx = next_net(idx)) {
         const TcNet nd = a.nets[a.order ? a.order[idx] : idx];
         const int H = nd.H;
         const int64_t n = nd.n;
@@ -561,7 +574,7 @@ void tc_fill_desc(void *desc, const void *tmap_dev, const float *y, float *param
 }
 
 cudaError_t tc_batched_train(const void *descs_dev, const int *order_dev, int n_nets, int D, int epochs, float lr,
-                             int loss_mean, int act, int *status, cudaStream_t st) {
+                             int loss_mean, int act, int *status, int *next, cudaStream_t st) {
     if (n_nets == 0 || epochs == 0) return cudaSuccess;
     auto kern = act == MLP_ACT_TANH ? k_tc_batched<MLP_ACT_TANH> : k_tc_batched<MLP_ACT_SIGMOID>;
     static bool attr_set[2] = {false, false};
@@ -581,6 +594,12 @@ cudaError_t tc_batched_train(const void *descs_dev, const int *order_dev, int n_
     a.act = act;
     a.status = status;
     const int grid = n_nets < device_sm_count() ? n_nets : device_sm_count();
+    a.next = nullptr;
+    if (next && n_nets > grid) {
+        cudaError_t e = cudaMemsetAsync(next, 0, sizeof(int), st);
+        if (e != cudaSuccess) return e;
+        a.next = next;
+    }
     kern<<<grid, NT, SM_ALLOC, st>>>(a);
     return cudaGetLastError();
 }
