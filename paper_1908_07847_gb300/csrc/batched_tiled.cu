@@ -67,8 +67,10 @@ __host__ __device__ inline TLayout t_layout(int D, int Hmax, int ncap, int hcap)
     L.HSS = L.HP + 4;
     L.xt = 0;                                   // X^T: 4 KQ rows x xs
     L.wt = L.xt + 4 * L.KQ * L.xs;              // W^T: 4 KQ rows x HP
-    L.hs = L.wt + 4 * L.KQ * L.HP;              // h / d1: hcap x HSS
-    L.w2 = L.hs + hcap * L.HSS;                 // w2: HP
+    L.hs = L.wt + 4 * L.KQ * L.HP;              // h / d1: hcap x HSS, and at least four rows at
+    const int hsz = hcap * L.HSS;               //   the widest stride a net can use (HSS + 4), so
+    const int hmin = 4 * (L.HSS + 4);           //   that a pass always takes at least four rows
+    L.w2 = L.hs + (hsz > hmin ? hsz : hmin);    // w2: HP
     L.d2 = L.w2 + L.HP;                         // d2: ncap (a pass never exceeds it)
     L.gwp = L.d2 + ncap;                        // gw2 partials: TNT x 4
     L.red = L.gwp + 4 * TNT;                    // reductions: 4 warps x (sse, gb2) + 4 doubles

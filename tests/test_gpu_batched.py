@@ -235,6 +235,21 @@ def test_kernel_shapes_match_oracle(shape):
         assert rel_err_norm(got[t], ref[t].flat()) <= W_TOL, ("tanh", shape, t)
 
 
+@pytest.mark.parametrize("shape", [0, 1, 2, 3, 4, 5, 6])
+def test_every_shape_on_plans_of_tiny_nets(shape):
+    """Plans whose widest net has at most 4 hidden units and whose nets have
+    at most 4 rows, on every kernel shape: in the register-tiled shapes the
+    smallest h / d1 buffer still takes at least four rows a pass (the layout
+    reserves four rows at the widest stride), against the oracle."""
+    for Hs, ns in (([1, 2, 3, 4], [1, 2, 3, 4]), ([1, 1], [4, 3]), ([2], [1])):
+        nets = make_batch(40 + len(Hs), Hs, ns)
+        got, gl = run_batch(nets, 20, shape=shape)
+        ref, rl = oracle.batch_train([(X, y, Params(*W)) for X, y, W in nets], lr32(), 20, threads=2)
+        for t in range(len(nets)):
+            assert rel_err_norm(got[t], ref[t].flat()) <= W_TOL, (shape, Hs[t], ns[t])
+            assert rel_err_elem(gl[t], rl[t]) <= 1e-5, (shape, Hs[t], ns[t])
+
+
 @pytest.mark.parametrize("shape", [1, 3])
 @pytest.mark.parametrize("D", [1, 5, 8, 16, 20, 32, 35, 36])
 def test_input_width_classes_of_the_other_shapes(D, shape):
