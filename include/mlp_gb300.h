@@ -281,7 +281,11 @@ mlp_status mlp_batch_create(int32_t prec, int32_t act, int32_t D,
 
 /* Train every net of the plan for `epochs` epochs: one kernel launch, no
  * allocation and no host synchronisation, so it can be captured in a CUDA
- * graph.  Each loss_hist must hold `epochs` doubles. */
+ * graph.  Each loss_hist must hold `epochs` doubles.  A plan runs one launch
+ * at a time: two launches of the same plan that overlap on the GPU train the
+ * same weights and, for MLP_BF16 plans, share the counter through which the
+ * plan's blocks take their nets (a small memset before the kernel, on
+ * `stream`, zeroes it). */
 mlp_status mlp_batch_run(mlp_batch_t b, int32_t epochs, void *stream);
 
 /* Synchronise `stream`, then return and clear the plan's device status
